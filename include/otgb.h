@@ -1,0 +1,199 @@
+/*
+ * otgb -- multiscale, symmetric, debiased Sinkhorn on one GB300 (sm_103a).
+ *
+ * C ABI of libotgb.so.  Method: Feydy, Roussillon, Trouve, Gori, "Fast and
+ * Scalable Optimal Transport for Brain Tractograms" (MICCAI 2019), Section 2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Arrays are DEVICE pointers (cudaMalloc'd, or torch CUDA tensors), owned by
+ *    the caller, row-major and contiguous: points are N x D float32, weights N
+ *    float32, labels int32.  The library never frees or retains them beyond
+ *    the call, except the non-owning views held by an otgb_plan (see below).
+ *  - Host pointers are marked "host".  Scalars are passed by value.
+ *  - All GPU work is enqueued on the context's CUDA stream.  A call returns
+ *    after its results are complete on that stream unless stated otherwise.
+ *  - Every function returns an otgb_status; on failure otgb_last_error() gives
+ *    a message.  No exception crosses the ABI and no kernel traps.
+ *  - Scratch memory comes from the context (stream-ordered allocations that
+ *    grow on demand) and is released by otgb_destroy().
+ *  - Ground cost: C(x, y) = |x - y|^2 / 2 (p = 2, Section 2).  Other p are
+ *    rejected with OTGB_EINVAL.  1 <= D <= 64.
+ */
+#ifndef OTGB_H
+#define OTGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OTGB_OK = 0,
+    OTGB_EINVAL = -1,     /* bad argument: shape, null pointer, blur <= 0, q not in (0,1), ... */
+    OTGB_ECUDA = -2,      /* a CUDA runtime call failed */
+    OTGB_ENOMEM = -3,     /* device scratch allocation failed */
+    OTGB_ENOCONV = -4,    /* max_iters reached before the stopping rule held (results still written) */
+    OTGB_ENONFINITE = -5, /* a potential or the divergence became NaN/Inf */
+    OTGB_ETIMEOUT = -6,   /* a bounded device-side wait gave up */
+    OTGB_EINTERNAL = -7   /* internal consistency check failed */
+} otgb_status;
+
+typedef enum { OTGB_FP32 = 0, OTGB_TC_BF16X3 = 1 } otgb_precision;
+typedef enum { OTGB_CLUSTER_GRID = 0, OTGB_CLUSTER_KMEANS = 1 } otgb_cluster_kind;
+
+/* Opaque handles. */
+typedef struct otgb_ctx otgb_ctx;   /* one device + one stream + scratch */
+typedef struct otgb_plan otgb_plan; /* result of a solve, reused by transport_apply */
+
+/* Solver parameters (Section 2: blur, reach, scaling; p = 2). */
+typedef struct {
+    int p;                 /* exponent of the cost; must be 2 */
+    double blur;           /* finest scale sigma; eps = blur^p.  > 0 */
+    double reach;          /* rho = reach^p; <= 0 or +inf: balanced OT (lambda = 1) */
+    double scaling;        /* q in (0,1): sigma_{k+1} = q sigma_k (the paper's default is 0.9) */
+    double diameter;       /* first sigma; <= 0: diagonal of the bounding box of x and y */
+    int multiscale;        /* 1: cluster, coarse solve, extrapolate, truncate; 0: dense single scale */
+    int cluster;           /* otgb_cluster_kind, used when multiscale = 1 */
+    double cell;           /* grid cell width (same units as x), cluster = GRID; D <= 3 */
+    int k_clusters;        /* k-means clusters per side, cluster = KMEANS */
+    int kmeans_iters;      /* Lloyd iterations (default 10) */
+    unsigned long long seed; /* seed of the k-means initial sample */
+    double sigma_switch;   /* last coarse scale; <= 0: the cluster scale (cell, or 2 x RMS cluster radius) */
+    double trunc_tau;      /* keep a cluster pair when its log plan bound >= -tau (default 27.6 = -log 1e-12) */
+    double tol;            /* stopping rule at sigma = blur: estimated remaining relative change of S < tol */
+    int min_iters;         /* at least this many steps at sigma = blur (default 3) */
+    int max_iters;         /* cap on the total number of steps, schedule included */
+    int check_every;       /* evaluate S and the stopping rule every k steps (default 10) */
+    int fixed_iters;       /* > 0: run exactly this many steps at sigma = blur after the schedule, no stopping rule */
+    int precision;         /* otgb_precision; OTGB_TC_BF16X3 only for D >= 16 */
+    /* Optional warm start (device, caller order), used as the initial values of the
+       four vectors when non-null; the schedule then starts at eps_start. */
+    const float *f_init, *g_init, *a_init, *b_init;
+    double sigma_start;    /* <= 0: the full schedule from the diameter */
+} otgb_params;
+
+/* Statistics of one solve (host struct, filled when non-null). */
+typedef struct {
+    int iters_total;         /* averaged steps, all phases */
+    int iters_coarse;        /* steps on the cluster measures */
+    int iters_fine;          /* steps at full resolution */
+    int n_clusters_x, n_clusters_y;
+    int schedule_len;
+    double diameter;
+    double sigma_switch;
+    double pairs_evaluated;  /* (i,j) terms computed by softmin kernels, all instances */
+    double pairs_dense;      /* (N^2 + M^2 + 2NM) per fine step, summed over fine steps */
+    double kept_fraction;    /* last fine step: evaluated / dense pairs */
+    double softmin_ms;       /* device time of the softmin kernels (CUDA events) */
+    double total_ms;         /* device time of the whole solve */
+    double last_delta;       /* last max |new - old| / eps over the four vectors */
+    double last_rel_change;  /* last estimated remaining relative change of S */
+    long long fallback_rows; /* rows recomputed by the safe two-pass kernel */
+} otgb_stats;
+
+/* Fill *p with defaults: p = 2, blur = 0.05, reach = 0 (balanced), scaling = 0.5,
+   multiscale = 0, cluster = GRID, kmeans_iters = 10, trunc_tau = 27.6, tol = 1e-6,
+   min_iters = 3, max_iters = 100000, check_every = 10, precision = FP32. */
+void otgb_default_params(otgb_params *p);
+
+/* Create a context on `device` that enqueues work on `cuda_stream`
+   (a cudaStream_t; NULL: the legacy default stream).  *out receives the handle. */
+int otgb_create(otgb_ctx **out, int device, void *cuda_stream);
+/* Release the context and all its scratch memory. */
+int otgb_destroy(otgb_ctx *ctx);
+/* Last error message of the context (static storage when ctx is NULL). */
+const char *otgb_last_error(const otgb_ctx *ctx);
+
+/*
+ * Debiased Sinkhorn divergence S_{eps,rho}(alpha, beta), Eq. (5) evaluated in
+ * its dual form Eq. (6), with the symmetric, averaged, eps-scaled loop of the
+ * Algorithm in Section 2 and, when params->multiscale = 1, the coarse-to-fine
+ * strategy of Section 2 (clustering, coarse solve, extrapolation of the duals
+ * by one softmin, kernel truncation of negligible cluster pairs).
+ *
+ *   x: N x D points, a: N weights (>= 0, positive total); y: M x D, b: M.
+ *   cost_host (host, required): receives S in double precision.
+ *   f (N), g (M): device outputs, the dual pair (f, g) = (b^{beta->alpha},
+ *     a^{alpha->beta}) of OT(alpha, beta), in the caller's point order.
+ *   a_self (N), b_self (M): optional device outputs, the symmetric duals of
+ *     OT(alpha, alpha) and OT(beta, beta).
+ *   plan_out: optional; receives a plan for transport_apply (free it with
+ *     otgb_plan_free).  The plan keeps NON-OWNING views of x, y and b: they must
+ *     stay valid until the plan is freed.
+ *   stats: optional host struct.
+ * Errors: EINVAL for N or M < 1, D outside [1, 64], p != 2, blur <= 0, q outside
+ * (0,1), negative or non-finite weights or a zero total mass; ENOCONV when
+ * max_iters ends the loop first (outputs are written); ENONFINITE when a
+ * potential turns NaN/Inf; ECUDA/ENOMEM from the runtime.
+ */
+int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a, int N, const float *y, const float *b,
+                        int M, int D, const otgb_params *params, double *cost_host, float *f, float *g,
+                        float *a_self, float *b_self, otgb_plan **plan_out, otgb_stats *stats);
+
+/*
+ * Label transfer through the smooth plan, Eq. (7):
+ *   Lab_il = sum_{j : labels_j = l} b_j exp((f_i + g_j - C(x_i, y_j)) / eps),
+ * eps = blur^p of the plan, i.e. (1/alpha_i)(pi l)_i with pi of Eq. (4).
+ *   f (N), g (M): device duals in the caller's order (normally the ones
+ *     sinkhorn_divergence wrote); labels: M int32 in [0, L) (others ignored).
+ *   scores: N x L float32 (optional), argmax: N int32 (lowest class on ties;
+ *     -1 when the row is empty), row_mass: N float32 = sum_l Lab_il (optional).
+ * A row whose mass is near 0 is an outlier (Section 2, label transfer).
+ * Truncated plans reuse the cluster-pair mask of the last fine step.
+ * Errors: EINVAL for a null plan, L < 1 or L > 1024, null f/g/labels/argmax.
+ */
+int transport_apply(otgb_ctx *ctx, const otgb_plan *plan, const float *f, const float *g, const int32_t *labels,
+                    int L, float *scores, int32_t *argmax, float *row_mass);
+void otgb_plan_free(otgb_plan *plan);
+
+/*
+ * Grid clustering (coarse subsampling, Section 2): cell coordinate
+ * floor((x_d - min_d x) / cell) per axis, evaluated in IEEE single precision;
+ * cells ordered by their Morton (bit-interleaved) key; points stably sorted by
+ * key.  D <= 3; at most 1024 cells per axis.
+ *   labels (N): cluster of each point (caller order).  perm (N): sorted position
+ *   -> original index.  offsets (capacity N+1): cluster k holds sorted positions
+ *   [offsets[k], offsets[k+1]).  n_clusters (host): number of clusters.
+ *   centroids (optional, capacity N x D): weighted mean of each cluster, with
+ *   weights w (optional, device, N; NULL = uniform).
+ * Errors: EINVAL for D > 3, cell <= 0, or more than 1024 cells along an axis.
+ */
+int cluster_grid(otgb_ctx *ctx, const float *x, const float *w, int N, int D, float cell, int32_t *labels,
+                 int32_t *perm, int32_t *offsets, int *n_clusters, float *centroids);
+
+/*
+ * Weighted K-means (Lloyd), the "simple K-means" of Section 2: K initial
+ * centroids sampled without replacement from x with a seeded generator, then
+ * `iters` rounds of nearest-centroid assignment and weighted-mean update (an
+ * empty cluster keeps its centroid), then a final assignment.  Points are then
+ * stably sorted by cluster.
+ *   labels (N), centroids (K x D), perm (N), offsets (K+1).  w optional (NULL =
+ *   uniform).  init (optional, device K x D) replaces the seeded sample.
+ * Errors: EINVAL for K < 1, K > N, D outside [1, 64].
+ */
+int cluster_kmeans(otgb_ctx *ctx, const float *x, const float *w, int N, int D, int K, int iters,
+                   unsigned long long seed, const float *init, int32_t *labels, float *centroids, int32_t *perm,
+                   int32_t *offsets);
+
+/*
+ * One softmin sweep of the Algorithm in Section 2, exposed for testing and for
+ * custom loops:
+ *   out_i = -lam * eps * log sum_k w_k exp((pot_k - C(p_k, q_i)) / eps)
+ * for rows q (n_out x D) and columns p (n_in x D) with weights w (n_in) and
+ * potential pot (n_in), dense.  When old is non-null the result is blended:
+ *   out_i <- old_i + omega (out_i - old_i)   (omega = 1/2 is the paper's average).
+ * Errors: EINVAL for sizes < 1, D outside [1, 64], eps <= 0.
+ */
+int otgb_softmin(otgb_ctx *ctx, const float *q, int n_out, const float *p, const float *w, const float *pot,
+                 int n_in, int D, double eps, double lam, const float *old, double omega, float *out);
+
+/* Number of CUDA kernels this library has launched in this process (all
+   contexts), for accounting by benchmarks. */
+unsigned long long otgb_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OTGB_H */

@@ -1,0 +1,234 @@
+// Weighted Lloyd K-means, the "simple K-means" coarse subsampling of
+// Section 2: seeded sample of K distinct points as initial centroids, then
+// rounds of nearest-centroid assignment (lowest index on ties) and
+// weighted-mean update (an empty cluster keeps its centroid), a final
+// assignment, and a stable sort of the points by cluster.
+#include <cfloat>
+#include <cmath>
+#include <unordered_set>
+#include <vector>
+
+#include "kmeans.cuh"
+#include "prims.cuh"
+#include "solver.cuh"
+
+namespace otgb {
+namespace {
+
+constexpr int kAT = 256;   // threads
+constexpr int kAR = 128;   // points per CTA
+constexpr int kAC = 64;    // centroids per tile
+
+// Nearest centroid by argmin_k (|c_k|^2 - 2 x.c_k): each thread keeps 8 points
+// x 4 centroids of dot products, register-tiled like a GEMM.
+struct AssignSmem {
+    float xs[64][kAR];
+    float cs[64][kAC];
+    float cn[kAC];
+    float bd[16][kAR];
+    int bk[16][kAR];
+};
+
+__global__ void __launch_bounds__(kAT) kmeans_assign_kernel(const float *x, int n, int D, int D4, const float *cent,
+                                                            int K, int *labels) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AssignSmem &S = *reinterpret_cast<AssignSmem *>(smem_raw);
+    const int t = threadIdx.x, r0 = blockIdx.x * kAR;
+    for (int e = t; e < kAR * D4; e += kAT) {
+        const int r = e / D4, k = e - r * D4;
+        S.xs[k][r] = (r0 + r < n && k < D) ? x[(size_t)(r0 + r) * D + k] : 0.f;
+    }
+    const int tr = t >> 4, tc = t & 15;
+    float best[8];
+    int bidx[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { best[i] = INFINITY; bidx[i] = 0x7fffffff; }
+    for (int c0 = 0; c0 < K; c0 += kAC) {
+        __syncthreads();
+        for (int e = t; e < kAC * D4; e += kAT) {
+            const int c = e / D4, k = e - c * D4;
+            S.cs[k][c] = (c0 + c < K && k < D) ? cent[(size_t)(c0 + c) * D4 + k] : 0.f;
+        }
+        __syncthreads();
+        if (t < kAC) {
+            float acc = 0.f;
+            for (int k = 0; k < D4; ++k) acc = fmaf(S.cs[k][t], S.cs[k][t], acc);
+            S.cn[t] = (c0 + t < K) ? acc : INFINITY;
+        }
+        __syncthreads();
+        float acc[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        for (int k = 0; k < D4; ++k) {
+            const float4 xa = *reinterpret_cast<const float4 *>(&S.xs[k][tr * 8]);
+            const float4 xb = *reinterpret_cast<const float4 *>(&S.xs[k][tr * 8 + 4]);
+            const float4 cv = *reinterpret_cast<const float4 *>(&S.cs[k][tc * 4]);
+            const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+            const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xv[i], cc[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = c0 + tc * 4 + j;
+            const float cn = S.cn[tc * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float d = fmaf(-2.f, acc[i][j], cn);
+                if (d < best[i] || (d == best[i] && c < bidx[i])) { best[i] = d; bidx[i] = c; }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { S.bd[tc][tr * 8 + i] = best[i]; S.bk[tc][tr * 8 + i] = bidx[i]; }
+    __syncthreads();
+    if (t < kAR && r0 + t < n) {
+        float b = S.bd[0][t];
+        int k = S.bk[0][t];
+        for (int q = 1; q < 16; ++q) {
+            const float d = S.bd[q][t];
+            const int kk = S.bk[q][t];
+            if (d < b || (d == b && kk < k)) { b = d; k = kk; }
+        }
+        labels[r0 + t] = k;
+    }
+}
+
+__global__ void kmeans_accum_kernel(const float *x, const float *w, int n, int D, const int *labels, float *sum,
+                                    float *mass, int D4) {
+    const int i = blockIdx.x, t = threadIdx.x;
+    if (i >= n) return;
+    const int k = labels[i];
+    const float wi = w ? w[i] : 1.f;
+    for (int d = t; d < D; d += blockDim.x) atomicAdd(&sum[(size_t)k * D4 + d], wi * x[(size_t)i * D + d]);
+    if (t == 0) atomicAdd(&mass[k], wi);
+}
+
+__global__ void kmeans_update_kernel(float *cent, const float *sum, const float *mass, int K, int D, int D4) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= K * D) return;
+    const int k = e / D, d = e - k * D;
+    if (mass[k] > 0.f) cent[(size_t)k * D4 + d] = sum[(size_t)k * D4 + d] / mass[k];
+}
+
+__global__ void gather_rows_kernel(const float *x, int D, const int *idx, int K, float *out, int D4) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= K * D4) return;
+    const int k = e / D4, d = e - k * D4;
+    out[e] = d < D ? x[(size_t)idx[k] * D + d] : 0.f;
+}
+
+__global__ void copy_rows_kernel(const float *src, int D, int K, float *out, int D4) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= K * D4) return;
+    const int k = e / D4, d = e - k * D4;
+    out[e] = d < D ? src[(size_t)k * D + d] : 0.f;
+}
+
+__global__ void label_keys_kernel(const int *labels, int n, uint32_t *keys, int *counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        keys[i] = (uint32_t)labels[i];
+        atomicAdd(&counts[labels[i]], 1);
+    }
+}
+
+__global__ void offsets_finish_kernel(const int *excl, const int *counts, int K, int *offsets) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < K) offsets[k] = excl[k];
+    if (k == K - 1) offsets[K] = excl[k] + counts[k];
+}
+
+uint64_t splitmix64(uint64_t &s) {
+    uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+// K distinct indices in [0, n) by Floyd's sampling with a splitmix64 stream.
+std::vector<int> sample_distinct(int n, int K, unsigned long long seed) {
+    std::vector<int> out;
+    std::unordered_set<int> used;
+    uint64_t s = seed;
+    for (int j = n - K; j < n; ++j) {
+        const int t = (int)(splitmix64(s) % (uint64_t)(j + 1));
+        if (used.count(t)) { used.insert(j); out.push_back(j); }
+        else { used.insert(t); out.push_back(t); }
+    }
+    return out;
+}
+
+void kmeans_assign(const float *x, int n, int D, const float *cent, int K, int *labels, cudaStream_t st) {
+    const int D4 = (D + 3) & ~3;
+    static bool attr = false;
+    if (!attr) {
+        OTGB_CUDA_TRY(cudaFuncSetAttribute(kmeans_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(AssignSmem)));
+        attr = true;
+    }
+    kmeans_assign_kernel<<<(n + kAR - 1) / kAR, kAT, sizeof(AssignSmem), st>>>(x, n, D, D4, cent, K, labels);
+    OTGB_CHECK_LAUNCH();
+}
+
+KmeansResult kmeans(otgb_ctx *ctx, const std::string &tag, const float *x, const float *w, int n, int D, int K,
+                    int iters, unsigned long long seed, const float *init) {
+    cudaStream_t st = ctx_stream(ctx);
+    Workspace &ws = ctx_ws(ctx);
+    const int D4 = (D + 3) & ~3;
+    KmeansResult r;
+    r.cstride = D4;
+    r.K = K;
+    r.centroids = ws.get<float>(tag + ":cent", (size_t)K * D4);
+    r.labels = ws.get<int>(tag + ":lab", n);
+    r.perm = ws.get<int>(tag + ":perm", n);
+    r.offsets = ws.get<int>(tag + ":off", K + 1);
+    if (init) {
+        copy_rows_kernel<<<(K * D4 + 255) / 256, 256, 0, st>>>(init, D, K, r.centroids, D4);
+        OTGB_CHECK_LAUNCH();
+    } else {
+        std::vector<int> idx = sample_distinct(n, K, seed);
+        int *d_idx = ws.get<int>(tag + ":idx", K);
+        OTGB_CUDA_TRY(cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * K, cudaMemcpyHostToDevice, st));
+        gather_rows_kernel<<<(K * D4 + 255) / 256, 256, 0, st>>>(x, D, d_idx, K, r.centroids, D4);
+        OTGB_CHECK_LAUNCH();
+        OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // idx is host memory about to go out of scope
+    }
+    float *sum = ws.get<float>(tag + ":sum", (size_t)K * D4);
+    float *mass = ws.get<float>(tag + ":mass", K);
+    for (int it = 0; it < iters; ++it) {
+        kmeans_assign(x, n, D, r.centroids, K, r.labels, st);
+        OTGB_CUDA_TRY(cudaMemsetAsync(sum, 0, sizeof(float) * (size_t)K * D4, st));
+        OTGB_CUDA_TRY(cudaMemsetAsync(mass, 0, sizeof(float) * K, st));
+        kmeans_accum_kernel<<<n, 64, 0, st>>>(x, w, n, D, r.labels, sum, mass, D4);
+        OTGB_CHECK_LAUNCH();
+        kmeans_update_kernel<<<(K * D + 255) / 256, 256, 0, st>>>(r.centroids, sum, mass, K, D, D4);
+        OTGB_CHECK_LAUNCH();
+    }
+    kmeans_assign(x, n, D, r.centroids, K, r.labels, st);
+    // stable sort by cluster and offsets of all K clusters (empty ones included)
+    uint32_t *keys = ws.get<uint32_t>(tag + ":keys", n);
+    int *counts = ws.get<int>(tag + ":cnt", K + 1);
+    int *excl = ws.get<int>(tag + ":excl", K + 1);
+    OTGB_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (K + 1), st));
+    label_keys_kernel<<<(n + 255) / 256, 256, 0, st>>>(r.labels, n, keys, counts);
+    OTGB_CHECK_LAUNCH();
+    int bits = 0;
+    while ((1 << bits) < K) ++bits;
+    void *scr = ws.get("sort:scratch", radix_sort_scratch_bytes(n));
+    radix_sort_pairs(keys, r.perm, n, bits, scr, st);
+    int *sscr = ws.get<int>("scan:scratch", scan_scratch_ints(K + 1) + 64);
+    exclusive_scan(counts, excl, K, sscr, st);
+    offsets_finish_kernel<<<(K + 255) / 256, 256, 0, st>>>(excl, counts, K, r.offsets);
+    OTGB_CHECK_LAUNCH();
+    r.sorted_keys = keys;
+    return r;
+}
+
+}  // namespace otgb

@@ -1,0 +1,80 @@
+// The solver state shared by the dense loop (sinkhorn.cu) and the
+// coarse-to-fine strategy (multiscale.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "otgb_internal.cuh"
+
+struct otgb_plan {
+    int N = 0, M = 0, D = 0;
+    const float *x = nullptr, *y = nullptr, *b = nullptr;  // non-owning views
+    double eps = 0.0;
+};
+
+namespace otgb {
+
+struct Cloud;
+struct Multiscale;
+
+struct Cloud {
+    int n = 0, D = 0, stride = 0;
+    float *pts = nullptr;   // n x stride, translated by the common centre
+    float *logw = nullptr;  // D > 3: log w (internal order)
+    float *w = nullptr;     // weights (internal order)
+    int *perm = nullptr;    // internal position -> caller index; null: identity
+    double mass = 0.0;
+};
+
+struct Solver {
+    static constexpr int kEvPool = 64;
+    otgb_ctx *ctx = nullptr;
+    cudaStream_t st = nullptr;
+    Workspace *ws = nullptr;
+    int D = 0;
+    double reach = 0.0, rho = 0.0;
+    Cloud X, Y;
+    std::vector<int> X_off, Y_off;  // cluster offsets (host) of the internal order, when clustered
+    float *pa[2] = {nullptr, nullptr}, *pf[2] = {nullptr, nullptr}, *pb[2] = {nullptr, nullptr},
+          *pg[2] = {nullptr, nullptr};
+    int cur = 0;
+    SoftminLaunch launch;
+    int rows_per_thread = 1, block_rows = 128;
+    unsigned long long *d_pairs = nullptr, *d_fb_total = nullptr;
+    int steps = 0, fine_steps = 0, coarse_steps = 0;
+    double S = 0.0, last_delta = 0.0, last_rel = 0.0, last_potmax = 0.0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    int ev_used = 0;
+    double softmin_ms = 0.0;
+    long softmin_launches = 0;
+    Multiscale *ms = nullptr;
+
+    ~Solver();
+    void alloc_common();
+    void alloc_pots(const otgb_params &P);
+    void setup_dense_instances(int block_rows);
+    void step(double sigma, bool count_pairs);
+    void fine_step(double sigma);
+    void harvest_timing();
+    double divergence(double eps);
+    int iterate_at_blur(const otgb_params &P, int it_budget);
+    static bool converged(const std::vector<double> &hist, double tol, double floor_abs, double *rem_out);
+    bool potentials_converged(double delta_prev, double delta, int m, double eps, double potmax, double tol) const;
+};
+
+std::vector<int> make_row_blocks(int n, int block_rows, const std::vector<int> *offsets);
+
+struct Multiscale {
+    double sigma_switch = 0.0;
+    int ncl_x = 0, ncl_y = 0;
+    double last_kept_fraction = 1.0;
+    void cluster(Solver &s, const otgb_params &P, const float *x, const float *a, const float *y, const float *b,
+                 const std::vector<float> &lox, const std::vector<float> &hix, const std::vector<float> &loy,
+                 const std::vector<float> &hiy, float *d_box);
+    int run_schedule(Solver &s, const otgb_params &P, const std::vector<double> &sched, int block_rows);
+    void before_fine_step(Solver &s, double sigma);
+};
+
+}  // namespace otgb

@@ -1,0 +1,141 @@
+// Internal declarations shared by the translation units of libotgb.so.
+// Device code targets sm_103a only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <cstdio>
+
+#include <string>
+#include <vector>
+
+#include "../../include/otgb.h"
+
+namespace otgb {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr double kLn2 = 0.69314718055994530942;
+
+// ---------------------------------------------------------------- errors ---
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define OTGB_STR2(x) #x
+#define OTGB_STR(x) OTGB_STR2(x)
+#define OTGB_CUDA_TRY(expr)                                                                          \
+    do {                                                                                             \
+        cudaError_t e_ = (expr);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            throw ::otgb::Error{OTGB_ECUDA, std::string(#expr) + " at " __FILE__ ":" OTGB_STR(__LINE__) \
+                                                ": " + cudaGetErrorString(e_)};                      \
+    } while (0)
+
+// After every launch: the launch error, and in debug mode (OTGB_DEBUG_SYNC=1 in
+// the environment) a device synchronisation that attributes a fault to the
+// launch site.
+bool debug_sync_enabled();
+#define OTGB_CHECK_LAUNCH()                                                    \
+    do {                                                                       \
+        OTGB_CUDA_TRY(cudaGetLastError());                                     \
+        if (::otgb::debug_sync_enabled()) OTGB_CUDA_TRY(cudaDeviceSynchronize()); \
+        ::otgb::count_launch();                                                \
+    } while (0)
+void count_launch();
+unsigned long long launch_count();
+
+// Opt-in device self-checks (compile with -DOTGB_CHECKED): an out-of-range
+// index is reported with printf and replaced by a safe one, so that the access
+// stays in bounds and control flow (barriers) is unchanged.
+#ifdef OTGB_CHECKED
+#define OTGB_DCLAMP(idx, lo, hi)                                                                        \
+    do {                                                                                                \
+        if ((idx) < (lo) || (idx) >= (hi)) {                                                            \
+            printf("OTGB_DCHECK %s:%d %s=%lld not in [%lld,%lld) block %d thread %d\n", __FILE__, __LINE__, \
+                   #idx, (long long)(idx), (long long)(lo), (long long)(hi), (int)blockIdx.x,           \
+                   (int)threadIdx.x);                                                                   \
+            (idx) = (lo);                                                                               \
+        }                                                                                               \
+    } while (0)
+#else
+#define OTGB_DCLAMP(idx, lo, hi) \
+    do {                         \
+    } while (0)
+#endif
+
+inline void require(bool ok, const std::string &msg, int code = OTGB_EINVAL) {
+    if (!ok) throw Error{code, msg};
+}
+
+// ------------------------------------------------------------- workspace ---
+// Stream-ordered scratch owned by a context.  Buffers are named so that a
+// repeated solve of the same size reuses them; growth reallocates.
+struct Workspace {
+    struct Buf {
+        std::string name;
+        void *ptr = nullptr;
+        size_t bytes = 0;
+    };
+    std::vector<Buf> bufs;
+    cudaStream_t stream = nullptr;
+    void *get(const std::string &name, size_t bytes);
+    template <class T> T *get(const std::string &name, size_t count) {
+        return static_cast<T *>(get(name, count * sizeof(T) + 16));
+    }
+    void release();
+};
+
+// --------------------------------------------------------------- softmin ---
+// One softmin instance: out_i = -lam eps log sum_{j in cols(i)} w_j exp((pot_j - C(p_j, q_i))/eps),
+// blended with the old value.  Rows and columns are stored in the solver's
+// internal (sorted, translated) order.
+//   D <= 3: rows/cols are float4 (x, y, z, unused) / (x, y, z, log w).
+//   D >  3: rows/cols are row-major with a stride of D4 = round_up(D, 4)
+//           floats; column log-weights sit in col_logw.
+struct SoftminInst {
+    const float *rows;       // n_rows points
+    const float *cols;       // n_cols points
+    const float *col_logw;   // D > 3 only: log w_j (-inf for w_j = 0)
+    const float *col_pot;    // potential on the columns (old values)
+    const float *row_old;    // old value of the output vector; null: no blend (out = tilde)
+    float *row_out;
+    int n_rows, n_cols;
+    float lam;               // damping 1/(1+eps/rho)
+    float omega;             // blend weight: out = old + omega (tilde - old)
+    // Row blocks and their column lists.  blk_row0[k]..blk_row0[k+1] are the rows
+    // of block k.  col_list == null: every block sees all columns (dense).
+    // Otherwise block k sees columns col_list[col_ptr[k] .. col_ptr[k+1]).
+    const int *blk_row0;
+    const int *col_ptr;
+    const int *col_list;
+};
+
+constexpr int kMaxInst = 4;
+
+struct SoftminLaunch {
+    SoftminInst inst[kMaxInst];
+    int n_inst;
+    const int2 *items;       // (instance, block) per CTA
+    int n_items;
+    float eps;               // temperature
+    float s;                 // log2(e) / eps
+    double eps_ln2;          // eps * ln 2 (double)
+    unsigned int *delta_max; // max |new - old| / eps as float bits (non-negative); may be null
+    int4 *fallback;          // (instance, row, block, 0) of rows needing the safe path
+    int *n_fallback;
+    int fallback_cap;
+    unsigned long long *fallback_total; // running count of fallback rows (may be null)
+    unsigned long long *pairs; // evaluated pair counter (may be null)
+};
+
+// Launch the fused softmin over all items of L, then the safe fallback for
+// any flagged rows (no host synchronisation; capturable in a CUDA graph).
+// D selects the specialisation.  Errors throw otgb::Error.
+void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_t st);
+
+// Build uniform row blocks of `block_rows` rows for an instance of n rows:
+// writes blk_row0 (n_blocks+1) on the device.  Returns n_blocks.
+int uniform_blocks(int *d_blk_row0, int n, int block_rows, cudaStream_t st);
+
+}  // namespace otgb

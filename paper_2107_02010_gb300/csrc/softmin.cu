@@ -1,0 +1,592 @@
+// Fused softmin kernels: the log-domain update of the Algorithm in Section 2,
+//
+//   tilde_i = -lam * eps * log sum_j w_j exp((pot_j - |q_i - p_j|^2 / 2) / eps)
+//   out_i   = old_i + omega (tilde_i - old_i)          (omega = 1/2: the paper's average)
+//
+// for up to four instances per launch (alpha<->alpha, beta<->beta, alpha->beta,
+// beta->alpha), dense or over the kept columns of each row block (the
+// block-sparse kernel truncation of Section 2).
+//
+// Arithmetic per pair.  Each CTA owns a block of rows; it picks a centre c (the
+// centre of the rows' bounding box, or their mean in high dimension) and works
+// in the shifted frame xt = x - c, yt = y - c, where
+//   -|xt - yt|^2/2 = -|xt|^2/2 - |yt|^2/2 + xt.yt.
+// The row term leaves the sum; per column the CTA stages, in shared memory,
+//   Y_j = s yt_j  and  H_j = s (eps log w_j + pot_j - |yt_j|^2 / 2),   s = log2(e)/eps,
+// and each row i carries a shift m_i, an estimate of its base-2 log-sum, so that
+// each (i, j) term is 2^((H_j - m_i) + xt_i . Y_j): one add, D FMAs, one MUFU
+// ex2, one add.  The shift comes from the old value of the row
+// (m_i = s (|xt_i|^2/2 - old_i/lam), exact at the fixed point), or, when there is
+// no old value, from a first pass that takes the exact maximum over the
+// columns.  A row whose sum ends outside [2^-60, 2^60] (the estimate was off by
+// more than 60 binades, so terms may have been flushed or may overflow) is
+// recomputed by the safe two-pass kernel in the direct form -|x - y|^2/2.
+// The per-row finish (log of the sum, the row term, the blend) is done in
+// double precision.
+#include <cfloat>
+#include <cmath>
+
+#include "otgb_internal.cuh"
+
+namespace otgb {
+namespace {
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 pack2(float lo, float hi) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(u64 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+template <int NT>
+__device__ __forceinline__ float block_max(float v, float *red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    float r = red[0];
+#pragma unroll
+    for (int k = 1; k < NT / 32; ++k) r = fmaxf(r, red[k]);
+    return r;
+}
+template <int NT>
+__device__ __forceinline__ float block_min(float v, float *red) {
+    return -block_max<NT>(-v, red);
+}
+
+// The row finish shared by all kernels.  L2 = log2 sum_j 2^(...) including K;
+// half_x2 = |xt_i|^2/2 (0 for the direct-difference fallback).
+__device__ __forceinline__ void finish_row(const SoftminLaunch &L, const SoftminInst &I, int r, double L2,
+                                           double half_x2, float &dmax) {
+    const double tilde = -(double)I.lam * (L.eps_ln2 * L2 - half_x2);
+    double nw = tilde;
+    if (I.row_old) {
+        const double old = (double)I.row_old[r];
+        nw = old + (double)I.omega * (tilde - old);
+        dmax = fmaxf(dmax, (float)(fabs(nw - old) / (double)L.eps));
+    }
+    I.row_out[r] = (float)nw;
+}
+
+__device__ __forceinline__ void push_fallback(const SoftminLaunch &L, int inst, int r, int blk) {
+    const int k = atomicAdd(L.n_fallback, 1);
+    if (k < L.fallback_cap) L.fallback[k] = make_int4(inst, r, blk, 0);
+}
+
+// ------------------------------------------------------------ D <= 3 ------
+// 128 threads; each owns R rows (rows t, t+128, ...).  With R >= 2 the rows
+// go in pairs through packed f32x2 FMAs.  Columns are staged 128 per tile as
+// (Y0,Y0,Y1,Y1 | Y2,Y2,H,H) so that one 16-byte shared load feeds a packed
+// operand pair.  TWO = true: exact-maximum first pass (no old value).
+constexpr int kNT3 = 128;
+constexpr int kT3 = 128;
+
+__device__ __forceinline__ bool row_sum_ok(float a) { return a >= 0x1p-60f && a <= 0x1p60f; }
+
+template <int R, bool TWO>
+__global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ SoftminLaunch L) {
+    __shared__ __align__(16) float4 tile[2][kT3][2];
+    __shared__ float red[kNT3 / 32];
+
+    int2 item = L.items[blockIdx.x];
+    OTGB_DCLAMP(item.x, 0, L.n_inst);
+    const SoftminInst &I = L.inst[item.x];
+    const int blk = item.y;
+    int r0 = I.blk_row0[blk], r1 = I.blk_row0[blk + 1];
+    OTGB_DCLAMP(r0, 0, I.n_rows + 1);
+    OTGB_DCLAMP(r1, r0, I.n_rows + 1);
+    const int t = threadIdx.x;
+    const float4 *rows4 = reinterpret_cast<const float4 *>(I.rows);
+    const float4 *cols4 = reinterpret_cast<const float4 *>(I.cols);
+    const float eps = L.eps, s = L.s;
+
+    // rows and the centre of their bounding box
+    float xr[R][3];
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int r = r0 + t + k * kNT3;
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < r1) {
+            p = rows4[r];
+            lo[0] = fminf(lo[0], p.x); hi[0] = fmaxf(hi[0], p.x);
+            lo[1] = fminf(lo[1], p.y); hi[1] = fmaxf(hi[1], p.y);
+            lo[2] = fminf(lo[2], p.z); hi[2] = fmaxf(hi[2], p.z);
+        }
+        xr[k][0] = p.x; xr[k][1] = p.y; xr[k][2] = p.z;
+    }
+    float c[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float l = block_min<kNT3>(lo[d], red);
+        const float h = block_max<kNT3>(hi[d], red);
+        c[d] = 0.5f * (l + h);
+    }
+    float m[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int r = r0 + t + k * kNT3;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) xr[k][d] = (r < r1) ? xr[k][d] - c[d] : 0.f;
+        m[k] = 0.f;
+        if (!TWO && r < r1) {
+            const double hx = 0.5 * ((double)xr[k][0] * xr[k][0] + (double)xr[k][1] * xr[k][1] +
+                                     (double)xr[k][2] * xr[k][2]);
+            m[k] = (float)((double)s * (hx - (double)I.row_old[r] / (double)I.lam));
+        }
+    }
+
+    // columns of this block
+    const int *list = I.col_list;
+    int c0 = 0, c1 = I.n_cols;
+    if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
+    const int ncol = c1 - c0;
+    const int ntiles = (ncol + kT3 - 1) / kT3;
+
+    // staging of one tile: thread t loads column p0 + t
+    auto load_col = [&](int p0, float4 &q, float &pot) {
+        const int p = p0 + t;
+        if (p < ncol) {
+            int j = list ? list[c0 + p] : p;
+            OTGB_DCLAMP(j, 0, I.n_cols);
+            q = cols4[j];
+            pot = I.col_pot[j];
+        } else {
+            q = make_float4(0.f, 0.f, 0.f, -INFINITY);
+            pot = 0.f;
+        }
+    };
+    auto store_col = [&](int buf, const float4 &q, float pot) {
+        const float y0 = q.x - c[0], y1 = q.y - c[1], y2 = q.z - c[2];
+        const float stuff = fmaf(eps, q.w, pot);
+        const float H = s * (stuff - 0.5f * (y0 * y0 + y1 * y1 + y2 * y2));
+        const float Y0 = s * y0, Y1 = s * y1, Y2 = s * y2;
+        tile[buf][t][0] = make_float4(Y0, Y0, Y1, Y1);
+        tile[buf][t][1] = make_float4(Y2, Y2, H, H);
+    };
+
+    constexpr int P = R / 2;  // packed row pairs
+    u64 X0[P > 0 ? P : 1], X1[P > 0 ? P : 1], X2[P > 0 ? P : 1];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        X0[p] = pack2(xr[2 * p][0], xr[2 * p + 1][0]);
+        X1[p] = pack2(xr[2 * p][1], xr[2 * p + 1][1]);
+        X2[p] = pack2(xr[2 * p][2], xr[2 * p + 1][2]);
+    }
+
+    float4 q;
+    float pot;
+    if constexpr (TWO) {
+        // first pass: exact maximum of the exponents of each row
+        float mx[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) mx[k] = -INFINITY;
+        if (ntiles > 0) { load_col(0, q, pot); store_col(0, q, pot); }
+        __syncthreads();
+        for (int tt = 0; tt < ntiles; ++tt) {
+            const int buf = tt & 1;
+            const bool more = tt + 1 < ntiles;
+            if (more) load_col((tt + 1) * kT3, q, pot);
+            const int n = min(kT3, ncol - tt * kT3);
+            for (int cc = 0; cc < n; ++cc) {
+                const float4 a = tile[buf][cc][0], b = tile[buf][cc][1];
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    float v = fmaf(xr[k][2], b.x, b.z);
+                    v = fmaf(xr[k][1], a.z, v);
+                    v = fmaf(xr[k][0], a.x, v);
+                    mx[k] = fmaxf(mx[k], v);
+                }
+            }
+            if (more) store_col(buf ^ 1, q, pot);
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) m[k] = mx[k] > -INFINITY ? mx[k] : 0.f;
+    }
+
+    float tot[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) tot[k] = 0.f;
+    u64 Mn[P > 0 ? P : 1];
+#pragma unroll
+    for (int p = 0; p < P; ++p) Mn[p] = pack2(-m[2 * p], -m[2 * p + 1]);
+
+    if (ntiles > 0) { load_col(0, q, pot); store_col(0, q, pot); }
+    __syncthreads();
+    for (int tt = 0; tt < ntiles; ++tt) {
+        const int buf = tt & 1;
+        const bool more = tt + 1 < ntiles;
+        if (more) load_col((tt + 1) * kT3, q, pot);
+        int n = min(kT3, ncol - tt * kT3);
+        n = (n + 3) & ~3;  // padded columns carry H = -inf
+        if constexpr (R >= 2) {
+            u64 acc[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) acc[p] = 0ull;
+            const ulonglong2 *tp = reinterpret_cast<const ulonglong2 *>(&tile[buf][0][0]);
+#pragma unroll 4
+            for (int cc = 0; cc < n; ++cc) {
+                const ulonglong2 a = tp[2 * cc], b = tp[2 * cc + 1];
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    u64 v = add2(b.y, Mn[p]);
+                    v = fma2(X2[p], b.x, v);
+                    v = fma2(X1[p], a.y, v);
+                    v = fma2(X0[p], a.x, v);
+                    float vl, vh;
+                    unpack2(v, vl, vh);
+                    acc[p] = add2(acc[p], pack2(ex2(vl), ex2(vh)));
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                float al, ah;
+                unpack2(acc[p], al, ah);
+                tot[2 * p] += al;
+                tot[2 * p + 1] += ah;
+            }
+        } else {
+            float acc = 0.f;
+#pragma unroll 4
+            for (int cc = 0; cc < n; ++cc) {
+                const float4 a = tile[buf][cc][0], b = tile[buf][cc][1];
+                float v = fmaf(xr[0][2], b.x, b.z - m[0]);
+                v = fmaf(xr[0][1], a.z, v);
+                v = fmaf(xr[0][0], a.x, v);
+                acc += ex2(v);
+            }
+            tot[0] += acc;
+        }
+        if (more) store_col(buf ^ 1, q, pot);
+        __syncthreads();
+    }
+
+    // per-row finish
+    float dmax = 0.f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int r = r0 + t + k * kNT3;
+        if (r >= r1) continue;
+        const float a = tot[k];
+        if (!row_sum_ok(a)) {
+            push_fallback(L, item.x, r, blk);
+            continue;
+        }
+        const double hx = 0.5 * ((double)xr[k][0] * xr[k][0] + (double)xr[k][1] * xr[k][1] +
+                                 (double)xr[k][2] * xr[k][2]);
+        finish_row(L, I, r, (double)m[k] + log2((double)a), hx, dmax);
+    }
+    dmax = block_max<kNT3>(dmax, red);
+    if (t == 0) {
+        if (L.delta_max) atomicMax(L.delta_max, __float_as_uint(dmax));
+        if (L.pairs) atomicAdd(L.pairs, (unsigned long long)(r1 - r0) * (unsigned long long)ncol);
+    }
+}
+
+// ------------------------------------------------------------ 3 < D <= 64 --
+// Register-tiled: 256 threads, a block of 128 rows times tiles of 64 columns;
+// each thread computes 8 rows x 4 columns.  Rows are staged once, k-major, as
+// X = s (x - c); column tiles are staged k-major as yt = y - c together with
+// H_j.  The accumulators start at H_j - m_i, so each pair costs D FMAs + one
+// add + ex2 + add.  TWO = true: an exact-maximum first pass over the columns.
+constexpr int kNTg = 256;
+constexpr int kBM = 128;
+constexpr int kBN = 64;
+
+struct GenSmem {
+    float xs[64][kBM];      // X, k-major
+    float ys[64][kBN];      // yt, k-major
+    float hs[kBN];          // H
+    float cen[64];
+    float hx[kBM];          // |xt|^2 / 2
+    float mrow[kBM];        // per-row shift m_i
+    float red[kNTg / 32];
+};
+
+template <bool TWO>
+__global__ void __launch_bounds__(kNTg) softmin_gen_kernel(const __grid_constant__ SoftminLaunch L, int D, int D4) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GenSmem &S = *reinterpret_cast<GenSmem *>(smem_raw);
+    int2 item = L.items[blockIdx.x];
+    OTGB_DCLAMP(item.x, 0, L.n_inst);
+    const SoftminInst &I = L.inst[item.x];
+    const int blk = item.y;
+    int r0 = I.blk_row0[blk], r1 = I.blk_row0[blk + 1];
+    OTGB_DCLAMP(r0, 0, I.n_rows + 1);
+    OTGB_DCLAMP(r1, r0, min(I.n_rows, r0 + kBM) + 1);
+    const int nr = r1 - r0;
+    const int t = threadIdx.x;
+    const float eps = L.eps, s = L.s;
+
+    // stage raw rows, k-major (zero beyond nr)
+    for (int e = t; e < kBM * D4; e += kNTg) {
+        const int r = e / D4, k = e - r * D4;
+        S.xs[k][r] = (r < nr) ? I.rows[(size_t)(r0 + r) * D4 + k] : 0.f;
+    }
+    __syncthreads();
+    // centre: per-coordinate mean of the block rows
+    for (int k = t; k < D4; k += kNTg) {
+        float acc = 0.f;
+        for (int r = 0; r < nr; ++r) acc += S.xs[k][r];
+        S.cen[k] = nr > 0 ? acc / (float)nr : 0.f;
+    }
+    __syncthreads();
+    for (int e = t; e < kBM * D4; e += kNTg) {
+        const int k = e / kBM, r = e - k * kBM;
+        S.xs[k][r] = (r < nr) ? S.xs[k][r] - S.cen[k] : 0.f;
+    }
+    __syncthreads();
+    if (t < kBM) {
+        float acc = 0.f;
+        for (int k = 0; k < D4; ++k) acc = fmaf(S.xs[k][t], S.xs[k][t], acc);
+        S.hx[t] = 0.5f * acc;
+        S.mrow[t] = 0.f;
+        if (!TWO && t < nr)
+            S.mrow[t] = (float)((double)s * ((double)(0.5f * acc) - (double)I.row_old[r0 + t] / (double)I.lam));
+    }
+    __syncthreads();
+    for (int e = t; e < kBM * D4; e += kNTg) {
+        const int k = e / kBM, r = e - k * kBM;
+        S.xs[k][r] *= s;
+    }
+
+    const int *list = I.col_list;
+    int c0 = 0, c1 = I.n_cols;
+    if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
+    const int ncol = c1 - c0;
+    const int tr = t >> 4, tc = t & 15;
+    const int ntiles = (ncol + kBN - 1) / kBN;
+    const int D44 = D4 >> 2;
+
+    auto stage = [&](int p0) {
+        __syncthreads();
+        for (int e = t; e < kBN * D44; e += kNTg) {
+            const int col = e % kBN, qq = e / kBN;
+            const int p = p0 + col;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (p < ncol) {
+                int j = list ? list[c0 + p] : p;
+                OTGB_DCLAMP(j, 0, I.n_cols);
+                v = *reinterpret_cast<const float4 *>(I.cols + (size_t)j * D4 + 4 * qq);
+                v.x -= S.cen[4 * qq]; v.y -= S.cen[4 * qq + 1]; v.z -= S.cen[4 * qq + 2]; v.w -= S.cen[4 * qq + 3];
+            }
+            S.ys[4 * qq][col] = v.x; S.ys[4 * qq + 1][col] = v.y; S.ys[4 * qq + 2][col] = v.z; S.ys[4 * qq + 3][col] = v.w;
+        }
+        __syncthreads();
+        if (t < kBN) {
+            const int p = p0 + t;
+            float acc = 0.f;
+            for (int k = 0; k < D4; ++k) acc = fmaf(S.ys[k][t], S.ys[k][t], acc);
+            float H = -INFINITY;
+            if (p < ncol) {
+                int j = list ? list[c0 + p] : p;
+                OTGB_DCLAMP(j, 0, I.n_cols);
+                const float stuff = fmaf(eps, I.col_logw[j], I.col_pot[j]);
+                H = s * (stuff - 0.5f * acc);
+            }
+            S.hs[t] = H;
+        }
+        __syncthreads();
+    };
+    auto dots = [&](float (&acc)[8][4]) {
+#pragma unroll 4
+        for (int k = 0; k < D4; ++k) {
+            const float4 xa = *reinterpret_cast<const float4 *>(&S.xs[k][tr * 8]);
+            const float4 xb = *reinterpret_cast<const float4 *>(&S.xs[k][tr * 8 + 4]);
+            const float4 yv = *reinterpret_cast<const float4 *>(&S.ys[k][tc * 4]);
+            const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+            const float yy[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(xv[i], yy[jj], acc[i][jj]);
+        }
+    };
+
+    if constexpr (TWO) {
+        float mx[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) mx[i] = -INFINITY;
+        for (int tt = 0; tt < ntiles; ++tt) {
+            stage(tt * kBN);
+            float acc[8][4];
+            const float4 h4 = *reinterpret_cast<const float4 *>(&S.hs[tc * 4]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { acc[i][0] = h4.x; acc[i][1] = h4.y; acc[i][2] = h4.z; acc[i][3] = h4.w; }
+            dots(acc);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                mx[i] = fmaxf(mx[i], fmaxf(fmaxf(acc[i][0], acc[i][1]), fmaxf(acc[i][2], acc[i][3])));
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            for (int o = 8; o > 0; o >>= 1) mx[i] = fmaxf(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], o));
+        __syncthreads();
+        if (tc == 0)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) S.mrow[tr * 8 + i] = mx[i] > -INFINITY ? mx[i] : 0.f;
+        __syncthreads();
+    }
+
+    float mreg[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mreg[i] = S.mrow[tr * 8 + i];
+    float rs[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rs[i] = 0.f;
+    for (int tt = 0; tt < ntiles; ++tt) {
+        stage(tt * kBN);
+        float acc[8][4];
+        const float4 h4 = *reinterpret_cast<const float4 *>(&S.hs[tc * 4]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            acc[i][0] = h4.x - mreg[i]; acc[i][1] = h4.y - mreg[i];
+            acc[i][2] = h4.z - mreg[i]; acc[i][3] = h4.w - mreg[i];
+        }
+        dots(acc);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) rs[i] += (ex2(acc[i][0]) + ex2(acc[i][1])) + (ex2(acc[i][2]) + ex2(acc[i][3]));
+    }
+    // reduce the 16 column-threads of each row group (lanes of one half-warp)
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        for (int o = 8; o > 0; o >>= 1) rs[i] += __shfl_xor_sync(0xffffffffu, rs[i], o);
+    float dmax = 0.f;
+    if (tc == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int rr = tr * 8 + i;
+            if (rr >= nr) continue;
+            const int r = r0 + rr;
+            const float a = rs[i];
+            if (!row_sum_ok(a)) {
+                push_fallback(L, item.x, r, blk);
+                continue;
+            }
+            finish_row(L, I, r, (double)mreg[i] + log2((double)a), (double)S.hx[rr], dmax);
+        }
+    }
+    dmax = block_max<kNTg>(dmax, S.red);
+    if (t == 0) {
+        if (L.delta_max) atomicMax(L.delta_max, __float_as_uint(dmax));
+        if (L.pairs) atomicAdd(L.pairs, (unsigned long long)nr * (unsigned long long)ncol);
+    }
+}
+
+// ------------------------------------------------------------- fallback ---
+// Rows flagged by the fast kernels, one warp per row (grid-stride over the
+// device-side count, so the launch needs no host synchronisation): two passes
+// over the row's columns in the direct form -|x - y|^2/2 (no cancellation),
+// max first, then the shifted sum.
+__global__ void softmin_fallback_kernel(const __grid_constant__ SoftminLaunch L, int D, int stride) {
+    const int count = min(*L.n_fallback, L.fallback_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && L.fallback_total && count > 0)
+        atomicAdd(L.fallback_total, (unsigned long long)count);
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += nw) {
+        int4 fb = L.fallback[w];
+        OTGB_DCLAMP(fb.x, 0, L.n_inst);
+        const SoftminInst &I = L.inst[fb.x];
+        OTGB_DCLAMP(fb.y, 0, I.n_rows);
+        const int r = fb.y, blk = fb.z;
+        const int *list = I.col_list;
+        int c0 = 0, c1 = I.n_cols;
+        if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
+        const float *xi = I.rows + (size_t)r * stride;
+        const float eps = L.eps, s = L.s;
+        auto term = [&](int p) -> float {
+            int j = list ? list[c0 + p] : p;
+            OTGB_DCLAMP(j, 0, I.n_cols);
+            const float *yj = I.cols + (size_t)j * stride;
+            float d2 = 0.f;
+            for (int k = 0; k < D; ++k) { const float t = xi[k] - yj[k]; d2 = fmaf(t, t, d2); }
+            const float lw = (D <= 3) ? yj[3] : I.col_logw[j];
+            return s * (fmaf(eps, lw, I.col_pot[j]) - 0.5f * d2);
+        };
+        float m = -INFINITY;
+        for (int p = lane; p < c1 - c0; p += 32) m = fmaxf(m, term(p));
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        double acc = 0.0;
+        if (m > -INFINITY)
+            for (int p = lane; p < c1 - c0; p += 32) acc += (double)exp2f(term(p) - m);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            float dmax = 0.f;
+            const double L2 = (m > -INFINITY) ? (double)m + log2(acc) : -INFINITY;
+            finish_row(L, I, r, L2, 0.0, dmax);
+            if (L.delta_max) atomicMax(L.delta_max, __float_as_uint(dmax));
+        }
+    }
+}
+
+__global__ void uniform_blocks_kernel(int *blk_row0, int n, int block_rows, int nb) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k <= nb) blk_row0[k] = min(k * block_rows, n);
+}
+
+}  // namespace
+
+int uniform_blocks(int *d_blk_row0, int n, int block_rows, cudaStream_t st) {
+    const int nb = (n + block_rows - 1) / block_rows;
+    uniform_blocks_kernel<<<(nb + 1 + 255) / 256, 256, 0, st>>>(d_blk_row0, n, block_rows, nb);
+    OTGB_CHECK_LAUNCH();
+    return nb;
+}
+
+void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_t st) {
+    if (L.n_items <= 0) return;
+    OTGB_CUDA_TRY(cudaMemsetAsync(L.n_fallback, 0, sizeof(int), st));
+    // the first-pass maximum is needed when some instance has no old value
+    bool two = false;
+    for (int k = 0; k < L.n_inst; ++k) two = two || (L.inst[k].row_old == nullptr);
+    if (D <= 3) {
+        switch (rows_per_thread + (two ? 8 : 0)) {
+            case 1: softmin3_kernel<1, false><<<L.n_items, kNT3, 0, st>>>(L); break;
+            case 2: softmin3_kernel<2, false><<<L.n_items, kNT3, 0, st>>>(L); break;
+            case 4: softmin3_kernel<4, false><<<L.n_items, kNT3, 0, st>>>(L); break;
+            case 9: softmin3_kernel<1, true><<<L.n_items, kNT3, 0, st>>>(L); break;
+            case 10: softmin3_kernel<2, true><<<L.n_items, kNT3, 0, st>>>(L); break;
+            default: softmin3_kernel<4, true><<<L.n_items, kNT3, 0, st>>>(L); break;
+        }
+    } else {
+        const int D4 = (D + 3) & ~3;
+        static bool attr = false;
+        if (!attr) {
+            OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sizeof(GenSmem)));
+            OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sizeof(GenSmem)));
+            attr = true;
+        }
+        if (two) softmin_gen_kernel<true><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
+        else softmin_gen_kernel<false><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
+    }
+    OTGB_CHECK_LAUNCH();
+    const int stride = D <= 3 ? 4 : ((D + 3) & ~3);
+    softmin_fallback_kernel<<<64, 256, 0, st>>>(L, D, stride);
+    OTGB_CHECK_LAUNCH();
+}
+
+}  // namespace otgb

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of libotgb.so (include/otgb.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors are torch CUDA tensors (device memory and streams come from
+PyTorch); the functions keep the C names.  The library must be built
+(``paper_2107_02010_gb300.build.build()``); there is no CPU fallback and a
+missing library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+_lib = None
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("p", C.c_int),
+        ("blur", C.c_double),
+        ("reach", C.c_double),
+        ("scaling", C.c_double),
+        ("diameter", C.c_double),
+        ("multiscale", C.c_int),
+        ("cluster", C.c_int),
+        ("cell", C.c_double),
+        ("k_clusters", C.c_int),
+        ("kmeans_iters", C.c_int),
+        ("seed", C.c_ulonglong),
+        ("sigma_switch", C.c_double),
+        ("trunc_tau", C.c_double),
+        ("tol", C.c_double),
+        ("min_iters", C.c_int),
+        ("max_iters", C.c_int),
+        ("check_every", C.c_int),
+        ("fixed_iters", C.c_int),
+        ("precision", C.c_int),
+        ("f_init", C.c_void_p),
+        ("g_init", C.c_void_p),
+        ("a_init", C.c_void_p),
+        ("b_init", C.c_void_p),
+        ("sigma_start", C.c_double),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("iters_total", C.c_int),
+        ("iters_coarse", C.c_int),
+        ("iters_fine", C.c_int),
+        ("n_clusters_x", C.c_int),
+        ("n_clusters_y", C.c_int),
+        ("schedule_len", C.c_int),
+        ("diameter", C.c_double),
+        ("sigma_switch", C.c_double),
+        ("pairs_evaluated", C.c_double),
+        ("pairs_dense", C.c_double),
+        ("kept_fraction", C.c_double),
+        ("softmin_ms", C.c_double),
+        ("total_ms", C.c_double),
+        ("last_delta", C.c_double),
+        ("last_rel_change", C.c_double),
+        ("fallback_rows", C.c_longlong),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+STATUS = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "ENOCONV", -5: "ENONFINITE", -6: "ETIMEOUT",
+          -7: "EINTERNAL"}
+
+EXPORTS = ["otgb_default_params", "otgb_create", "otgb_destroy", "otgb_last_error", "sinkhorn_divergence",
+           "transport_apply", "otgb_plan_free", "cluster_grid", "cluster_kmeans", "otgb_softmin",
+           "otgb_kernel_launches"]
+
+
+def kernel_launches() -> int:
+    return int(load().otgb_kernel_launches())
+
+
+class OtgbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libotgb.so (building it first if asked).  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libotgb.so is not built; run paper_2107_02010_gb300.build.build()")
+    lib = C.CDLL(_build.LIB)
+    vp, ci, cd = C.c_void_p, C.c_int, C.c_double
+    lib.otgb_default_params.argtypes = [C.POINTER(Params)]
+    lib.otgb_default_params.restype = None
+    lib.otgb_create.argtypes = [C.POINTER(vp), ci, vp]
+    lib.otgb_destroy.argtypes = [vp]
+    lib.otgb_last_error.argtypes = [vp]
+    lib.otgb_last_error.restype = C.c_char_p
+    lib.sinkhorn_divergence.argtypes = [vp, vp, vp, ci, vp, vp, ci, ci, C.POINTER(Params), C.POINTER(cd), vp, vp,
+                                        vp, vp, C.POINTER(vp), C.POINTER(Stats)]
+    lib.transport_apply.argtypes = [vp, vp, vp, vp, vp, ci, vp, vp, vp]
+    lib.otgb_plan_free.argtypes = [vp]
+    lib.otgb_plan_free.restype = None
+    lib.cluster_grid.argtypes = [vp, vp, vp, ci, ci, C.c_float, vp, vp, vp, C.POINTER(ci), vp]
+    lib.cluster_kmeans.argtypes = [vp, vp, vp, ci, ci, ci, ci, C.c_ulonglong, vp, vp, vp, vp, vp]
+    lib.otgb_softmin.argtypes = [vp, vp, ci, vp, vp, vp, ci, ci, cd, cd, vp, cd, vp]
+    lib.otgb_kernel_launches.argtypes = []
+    lib.otgb_kernel_launches.restype = C.c_ulonglong
+    for name in ("otgb_create", "otgb_destroy", "sinkhorn_divergence", "transport_apply", "cluster_grid",
+                 "cluster_kmeans", "otgb_softmin"):
+        getattr(lib, name).restype = ci
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _f32(t):
+    if t.dtype != torch.float32:
+        raise TypeError("expected float32, got %s" % t.dtype)
+    return _ptr(t)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().otgb_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """An otgb context bound to the current CUDA device and stream."""
+
+    def __init__(self, device=None, stream=None):
+        lib = load()
+        dev = torch.cuda.current_device() if device is None else int(device)
+        st = torch.cuda.current_stream(dev) if stream is None else stream
+        self.stream = st
+        h = C.c_void_p()
+        rc = lib.otgb_create(C.byref(h), dev, C.c_void_p(st.cuda_stream))
+        if rc != 0:
+            raise OtgbError(rc, lib.otgb_last_error(None).decode())
+        self.h = h
+
+    def check(self, rc):
+        if rc != 0:
+            raise OtgbError(rc, load().otgb_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().otgb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    def __init__(self, handle, keep):
+        self.h = handle
+        self._keep = keep  # the non-owning views must outlive the plan
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            load().otgb_plan_free(self.h)
+            self.h = None
+
+
+def sinkhorn_divergence(ctx: Context, x, a, y, b, params: Params | None = None, want_self=False,
+                        want_plan=False, want_stats=True, raise_on_noconv=True):
+    """Returns dict(S, f, g, [a_self, b_self], [plan], [stats], status)."""
+    N, D = x.shape
+    M = y.shape[0]
+    f = torch.empty(N, device=x.device, dtype=torch.float32)
+    g = torch.empty(M, device=x.device, dtype=torch.float32)
+    aa = torch.empty(N, device=x.device, dtype=torch.float32) if want_self else None
+    bb = torch.empty(M, device=x.device, dtype=torch.float32) if want_self else None
+    cost = C.c_double()
+    plan = C.c_void_p() if want_plan else None
+    st = Stats() if want_stats else None
+    p = params if params is not None else default_params()
+    rc = load().sinkhorn_divergence(ctx.h, _f32(x), _f32(a), N, _f32(y), _f32(b), M, D, C.byref(p), C.byref(cost),
+                                    _ptr(f), _ptr(g), _ptr(aa), _ptr(bb),
+                                    C.byref(plan) if plan is not None else None,
+                                    C.byref(st) if st is not None else None)
+    if rc != 0 and not (rc == -4 and not raise_on_noconv):
+        ctx.check(rc)
+    out = dict(S=cost.value, f=f, g=g, status=rc)
+    if want_self:
+        out["a_self"], out["b_self"] = aa, bb
+    if want_plan:
+        out["plan"] = Plan(plan, (x, y, b))
+    if want_stats:
+        out["stats"] = st.as_dict()
+    return out
+
+
+def transport_apply(ctx: Context, plan: Plan, f, g, labels, L, want_scores=True):
+    N = f.shape[0]
+    sc = torch.empty((N, L), device=f.device, dtype=torch.float32) if want_scores else None
+    am = torch.empty(N, device=f.device, dtype=torch.int32)
+    rm = torch.empty(N, device=f.device, dtype=torch.float32)
+    if labels.dtype != torch.int32:
+        raise TypeError("labels must be int32")
+    ctx.check(load().transport_apply(ctx.h, plan.h, _f32(f), _f32(g), _ptr(labels), int(L), _ptr(sc), _ptr(am),
+                                     _ptr(rm)))
+    return sc, am, rm
+
+
+def cluster_grid(ctx: Context, x, cell, w=None, want_centroids=True):
+    N, D = x.shape
+    labels = torch.empty(N, device=x.device, dtype=torch.int32)
+    perm = torch.empty(N, device=x.device, dtype=torch.int32)
+    offsets = torch.empty(N + 1, device=x.device, dtype=torch.int32)
+    cent = torch.empty((N, D), device=x.device, dtype=torch.float32) if want_centroids else None
+    n = C.c_int()
+    ctx.check(load().cluster_grid(ctx.h, _f32(x), _f32(w) if w is not None else None, N, D, float(cell),
+                                  _ptr(labels), _ptr(perm), _ptr(offsets), C.byref(n), _ptr(cent)))
+    k = n.value
+    return labels, perm, offsets[: k + 1], (cent[:k] if cent is not None else None)
+
+
+def cluster_kmeans(ctx: Context, x, K, iters=10, seed=0, w=None, init=None):
+    N, D = x.shape
+    labels = torch.empty(N, device=x.device, dtype=torch.int32)
+    cent = torch.empty((K, D), device=x.device, dtype=torch.float32)
+    perm = torch.empty(N, device=x.device, dtype=torch.int32)
+    offsets = torch.empty(K + 1, device=x.device, dtype=torch.int32)
+    ctx.check(load().cluster_kmeans(ctx.h, _f32(x), _f32(w) if w is not None else None, N, D, int(K), int(iters),
+                                    int(seed), _f32(init) if init is not None else None, _ptr(labels), _ptr(cent),
+                                    _ptr(perm), _ptr(offsets)))
+    return labels, cent, perm, offsets
+
+
+def softmin(ctx: Context, q, p, w, pot, eps, lam=1.0, old=None, omega=0.5):
+    n_out, D = q.shape
+    out = torch.empty(n_out, device=q.device, dtype=torch.float32)
+    ctx.check(load().otgb_softmin(ctx.h, _f32(q), n_out, _f32(p), _f32(w), _f32(pot), p.shape[0], D, float(eps),
+                                  float(lam), _f32(old) if old is not None else None, float(omega), _ptr(out)))
+    return out
