@@ -72,6 +72,14 @@ typedef struct {
        four vectors when non-null; the schedule then starts at eps_start. */
     const float *f_init, *g_init, *a_init, *b_init;
     double sigma_start;    /* <= 0: the full schedule from the diameter */
+    int translation;       /* unbalanced only: 1 = after every full-resolution step, move (f, g) to
+                              (f + c, -c + g) with c = (rho/2) log(<alpha, e^{-f/rho}> / <beta, e^{-g/rho}>),
+                              the exact dual ascent along the one direction the averaged loop contracts
+                              slowly (rate (1 + lambda)/2); the fixed point is unchanged (c = 0 there).
+                              0 = the paper's loop unchanged.  Default 1. */
+    int anderson;          /* > 0: Anderson acceleration with this history length (<= 8) of the steps at
+                              sigma = blur (Walker & Ni 2011); the fixed point is unchanged.  0: off.
+                              Default 5. */
 } otgb_params;
 
 /* Statistics of one solve (host struct, filled when non-null). */
@@ -95,7 +103,8 @@ typedef struct {
 
 /* Fill *p with defaults: p = 2, blur = 0.05, reach = 0 (balanced), scaling = 0.5,
    multiscale = 0, cluster = GRID, kmeans_iters = 10, trunc_tau = 27.6, tol = 1e-6,
-   min_iters = 3, max_iters = 100000, check_every = 10, precision = FP32. */
+   min_iters = 3, max_iters = 100000, check_every = 10, precision = FP32, translation = 1,
+   anderson = 5. */
 void otgb_default_params(otgb_params *p);
 
 /* Create a context on `device` that enqueues work on `cuda_stream`

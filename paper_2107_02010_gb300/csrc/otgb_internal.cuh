@@ -113,11 +113,24 @@ struct SoftminInst {
 
 constexpr int kMaxInst = 4;
 
+// Work decomposition: one CTA per item (inst, blk, cb, ce) = the rows of
+// block blk of instance inst against the positions [cb, ce) of the block's
+// column sequence.  When a block's columns are split over several items, each
+// item writes its per-row partial sums (same per-row shift in every item) to
+// part[item * kPartRows + local row] and a finalize CTA per block, listed in
+// fin as (inst, blk, first item, item count), sums them in a fixed order and
+// finishes the rows.  Only the D <= 3 kernel splits.
+constexpr int kPartRows = 512;
+
 struct SoftminLaunch {
     SoftminInst inst[kMaxInst];
     int n_inst;
-    const int2 *items;       // (instance, block) per CTA
+    const int4 *items;       // (instance, block, cb, ce) per CTA
     int n_items;
+    float *part;             // null: every block is a single item, finished inline
+    int exact_max;           // 1: take each row's shift from an exact maximum pass even when old values exist
+    const int4 *fin;         // finalize list (split mode)
+    int n_fin;
     float eps;               // temperature
     float s;                 // log2(e) / eps
     double eps_ln2;          // eps * ln 2 (double)

@@ -85,6 +85,44 @@ __global__ void divsum_final_kernel(const double *part, int nblk, double rho, do
     *out = balanced ? acc : -(rho + 0.5 * eps) * acc;
 }
 
+// ----------------------------------------------- translation of (f, g) ----
+// part[b] = (sum_i a_i e^{-f_i/rho}, sum_j b_j e^{-g_j/rho}) over a grid-stride share.
+__global__ void transl_partial_kernel(const float *wa, const float *f, int N, const float *wb, const float *g, int M,
+                                      double rho, double2 *part) {
+    __shared__ double sa[kRB], sb[kRB];
+    double A = 0.0, B = 0.0;
+    for (int i = blockIdx.x * kRB + threadIdx.x; i < N; i += gridDim.x * kRB) A += (double)wa[i] * exp(-(double)f[i] / rho);
+    for (int j = blockIdx.x * kRB + threadIdx.x; j < M; j += gridDim.x * kRB) B += (double)wb[j] * exp(-(double)g[j] / rho);
+    sa[threadIdx.x] = A;
+    sb[threadIdx.x] = B;
+    __syncthreads();
+    for (int o = kRB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) { sa[threadIdx.x] += sa[threadIdx.x + o]; sb[threadIdx.x] += sb[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sa[0], sb[0]);
+}
+
+// c = (rho/2) log(A/B) from the partial sums (fixed order), then f += c, g -= c.
+__global__ void transl_apply_kernel(const double2 *part, int nblk, double rho, float *f, int N, float *g, int M,
+                                    double *c_out) {
+    __shared__ float cs;
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0;
+        for (int b = 0; b < nblk; ++b) { A += part[b].x; B += part[b].y; }
+        double c = (A > 0.0 && B > 0.0) ? 0.5 * rho * log(A / B) : 0.0;
+        if (!isfinite(c)) c = 0.0;
+        cs = (float)c;
+        if (blockIdx.x == 0 && c_out) *c_out = c;
+    }
+    __syncthreads();
+    const float c = cs;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N + M; i += gridDim.x * blockDim.x) {
+        if (i < N) f[i] += c;
+        else g[i - N] -= c;
+    }
+}
+
 // ------------------------------------------------------------------- scan --
 constexpr int kScanB = 1024;
 
@@ -329,6 +367,15 @@ void divergence_sum(const float *wa, const float *f, const float *aa, int N, con
     divsum_partial_kernel<<<nblk, kRB, 0, st>>>(wa, f, aa, N, wb, g, bb, M, rho, balanced, d_part);
     OTGB_CHECK_LAUNCH();
     divsum_final_kernel<<<1, 32, 0, st>>>(d_part, nblk, rho, eps, balanced, d_out);
+    OTGB_CHECK_LAUNCH();
+}
+
+void translate_duals(const float *wa, float *f, int N, const float *wb, float *g, int M, double rho, double2 *d_part,
+                     double *d_c, cudaStream_t st) {
+    const int nblk = 64;
+    transl_partial_kernel<<<nblk, kRB, 0, st>>>(wa, f, N, wb, g, M, rho, d_part);
+    OTGB_CHECK_LAUNCH();
+    transl_apply_kernel<<<128, 256, 0, st>>>(d_part, nblk, rho, f, N, g, M, d_c);
     OTGB_CHECK_LAUNCH();
 }
 

@@ -15,6 +15,11 @@ void divergence_sum(const float *wa, const float *f, const float *aa, int N, con
                     const float *bb, int M, double eps, double rho, double *d_out, double *d_part,
                     cudaStream_t st);
 
+// Translation step of the cross duals (unbalanced): c = (rho/2) log(<a, e^{-f/rho}> / <b, e^{-g/rho}>),
+// f += c, g -= c, in place.  d_part: 64 double2; *d_c receives c (may be null).
+void translate_duals(const float *wa, float *f, int N, const float *wb, float *g, int M, double rho, double2 *d_part,
+                     double *d_c, cudaStream_t st);
+
 size_t scan_scratch_ints(int n);
 size_t scan_scratch_ints_level(int nb);
 // Exclusive prefix sum of n ints; scratch of scan_scratch_ints(n) ints.

@@ -3,6 +3,8 @@
 // Eq. (5) returned through its dual form Eq. (6).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 
@@ -12,6 +14,15 @@
 #include "solver.cuh"
 
 namespace otgb {
+
+bool trace_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("OTGB_TRACE");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
 
 namespace {
 
@@ -126,9 +137,9 @@ void Solver::harvest_timing() {
 }
 
 double Solver::divergence(double eps) {
-    double *dS = ws->get<double>("S", 1);
-    double *dpart = ws->get<double>("Spart", 128);
-    unsigned *dmax = ws->get<unsigned>("potmax", 1);
+    double *dS = ws->get<double>(nm("S"), 1);
+    double *dpart = ws->get<double>(nm("Spart"), 128);
+    unsigned *dmax = ws->get<unsigned>(nm("potmax"), 1);
     divergence_sum(X.w, pf[cur], pa[cur], X.n, Y.w, pg[cur], pb[cur], Y.n, eps, rho, dS, dpart, st);
     OTGB_CUDA_TRY(cudaMemsetAsync(dmax, 0, sizeof(unsigned), st));
     absmax(pf[cur], X.n, dmax, st);
@@ -165,28 +176,15 @@ std::vector<int> make_row_blocks(int n, int block_rows, const std::vector<int> *
     return b;
 }
 
-void Solver::setup_dense_instances(int block_rows) {
-    std::vector<int> hx = make_row_blocks(X.n, block_rows, X_off.empty() ? nullptr : &X_off);
-    std::vector<int> hy = make_row_blocks(Y.n, block_rows, Y_off.empty() ? nullptr : &Y_off);
-    int *bx = ws->get<int>("blk:x", hx.size());
-    int *by = ws->get<int>("blk:y", hy.size());
+void Solver::setup_instances(const std::vector<int> &hx, const std::vector<int> &hy) {
+    int *bx = ws->get<int>(nm("blk:x"), hx.size());
+    int *by = ws->get<int>(nm("blk:y"), hy.size());
     OTGB_CUDA_TRY(cudaMemcpyAsync(bx, hx.data(), hx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     OTGB_CUDA_TRY(cudaMemcpyAsync(by, hy.data(), hy.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    const int nbx = (int)hx.size() - 1, nby = (int)hy.size() - 1;
-    std::vector<int2> items;
-    const int rows_x[4] = {1, 0, 0, 1};  // instances 0 and 3 have x rows
-    for (int k = 0; k < 4; ++k) {
-        const int nb = rows_x[k] ? nbx : nby;
-        for (int bl = 0; bl < nb; ++bl) items.push_back(make_int2(k, bl));
-    }
-    int2 *d_items = ws->get<int2>("items", items.size());
-    OTGB_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
-    OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors go out of scope
     SoftminLaunch &L = launch;
     L.n_inst = 4;
-    L.items = d_items;
-    L.n_items = (int)items.size();
     const Cloud *rows[4] = {&X, &Y, &Y, &X}, *cols[4] = {&X, &Y, &X, &Y};
+    const int rows_x[4] = {1, 0, 0, 1};  // instances 0 and 3 have x rows
     for (int k = 0; k < 4; ++k) {
         SoftminInst &I = L.inst[k];
         I.rows = rows[k]->pts;
@@ -198,18 +196,73 @@ void Solver::setup_dense_instances(int block_rows) {
         I.col_ptr = nullptr;
         I.col_list = nullptr;
     }
+    nblk_x = (int)hx.size() - 1;
+    nblk_y = (int)hy.size() - 1;
+}
+
+void Solver::setup_dense_instances(int block_rows) {
+    std::vector<int> hx = make_row_blocks(X.n, block_rows, X_off.empty() ? nullptr : &X_off);
+    std::vector<int> hy = make_row_blocks(Y.n, block_rows, Y_off.empty() ? nullptr : &Y_off);
+    setup_instances(hx, hy);
+    std::vector<std::vector<int>> ncols(4);
+    const int rows_x[4] = {1, 0, 0, 1};
+    for (int k = 0; k < 4; ++k) ncols[k].assign(rows_x[k] ? nblk_x : nblk_y, launch.inst[k].n_cols);
+    set_work(ncols, D <= 3);
+}
+
+// Items (inst, blk, cb, ce): a block's columns are cut into chunks of CH
+// positions, CH chosen so that the launch has about three waves of CTAs
+// (six resident per SM); every block of a split launch goes through the
+// finalize pass, which sums its items' partial sums in item order.
+void Solver::set_work(const std::vector<std::vector<int>> &ncols, bool allow_split) {
+    const int sms = ctx_sm_count(ctx);
+    double W = 0.0;
+    for (auto &v : ncols)
+        for (int c : v) W += c;
+    const double target = 3.0 * 6.0 * sms;
+    int CH = 1 << 30;
+    if (allow_split) {
+        CH = (int)std::ceil(W / target);
+        CH = std::max(512, (CH + 127) / 128 * 128);
+    }
+    std::vector<int4> items, fin;
+    for (int k = 0; k < (int)ncols.size(); ++k)
+        for (int b = 0; b < (int)ncols[k].size(); ++b) {
+            const int n = ncols[k][b];
+            const int first = (int)items.size();
+            if (n <= CH) items.push_back(make_int4(k, b, 0, n));
+            else
+                for (int c = 0; c < n; c += CH) items.push_back(make_int4(k, b, c, std::min(n, c + CH)));
+            fin.push_back(make_int4(k, b, first, (int)items.size() - first));
+        }
+    const bool split = items.size() > fin.size();
+    int4 *d_items = ws->get<int4>(nm("items"), items.size() + 1);
+    OTGB_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    launch.items = d_items;
+    launch.n_items = (int)items.size();
+    launch.part = nullptr;
+    launch.fin = nullptr;
+    launch.n_fin = 0;
+    if (split) {
+        int4 *d_fin = ws->get<int4>(nm("fin"), fin.size() + 1);
+        OTGB_CUDA_TRY(cudaMemcpyAsync(d_fin, fin.data(), fin.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+        launch.part = ws->get<float>(nm("part"), items.size() * (size_t)kPartRows);
+        launch.fin = d_fin;
+        launch.n_fin = (int)fin.size();
+    }
+    OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors go out of scope
 }
 
 void Solver::alloc_common() {
     launch = SoftminLaunch();
-    launch.delta_max = ws->get<unsigned>("delta", 1);
+    launch.delta_max = ws->get<unsigned>(nm("delta"), 1);
     const int cap = 2 * (X.n + Y.n) + 64;
-    launch.fallback = ws->get<int4>("fb", cap);
-    launch.n_fallback = ws->get<int>("nfb", 1);
+    launch.fallback = ws->get<int4>(nm("fb"), cap);
+    launch.n_fallback = ws->get<int>(nm("nfb"), 1);
     launch.fallback_cap = cap;
-    d_fb_total = ws->get<unsigned long long>("fbtot", 1);
+    d_fb_total = ws->get<unsigned long long>(nm("fbtot"), 1);
     launch.fallback_total = d_fb_total;
-    d_pairs = ws->get<unsigned long long>("pairs", 1);
+    d_pairs = ws->get<unsigned long long>(nm("pairs"), 1);
     OTGB_CUDA_TRY(cudaMemsetAsync(d_fb_total, 0, sizeof(unsigned long long), st));
     OTGB_CUDA_TRY(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
     if (timing && ev_pool.empty()) {
@@ -225,10 +278,11 @@ Solver::~Solver() {
 
 void Solver::alloc_pots(const otgb_params &P) {
     for (int k = 0; k < 2; ++k) {
-        pa[k] = ws->get<float>("pa" + std::to_string(k), X.n);
-        pf[k] = ws->get<float>("pf" + std::to_string(k), X.n);
-        pb[k] = ws->get<float>("pb" + std::to_string(k), Y.n);
-        pg[k] = ws->get<float>("pg" + std::to_string(k), Y.n);
+        Z[k] = ws->get<float>(nm("Z" + std::to_string(k)), 2 * (size_t)X.n + 2 * (size_t)Y.n);
+        pa[k] = Z[k];
+        pf[k] = Z[k] + X.n;
+        pb[k] = Z[k] + 2 * (size_t)X.n;
+        pg[k] = Z[k] + 2 * (size_t)X.n + Y.n;
     }
     cur = 0;
     auto init = [&](float *dst, const float *src, const int *perm, int n) {
@@ -257,25 +311,36 @@ bool Solver::converged(const std::vector<double> &hist, double tol, double floor
     const size_t k = hist.size();
     if (k < 3) return false;
     const double d1 = hist[k - 1] - hist[k - 2], d0 = hist[k - 2] - hist[k - 3];
+    const double Sa = std::fabs(hist[k - 1]);
     double rem = std::fabs(d1);
     if (d0 != 0.0) {
         const double r = d1 / d0;
         if (r > 0.0 && r < 1.0) rem = std::fabs(d1) * r / (1.0 - r);
     }
-    if (rem_out) *rem_out = rem / std::max(std::fabs(hist[k - 1]), 1e-300);
-    return rem <= tol * std::fabs(hist[k - 1]) + floor_abs;
+    if (rem_out) *rem_out = rem / std::max(Sa, 1e-300);
+    // two successive increments at the float32 rounding level of S also satisfy the S rule
+    if (std::fabs(d1) <= 1e-7 * Sa && std::fabs(d0) <= 1e-7 * Sa) return true;
+    return rem <= tol * Sa + floor_abs;
 }
 
 bool Solver::potentials_converged(double delta_prev, double delta, int m, double eps, double potmax,
-                                  double tol) const {
+                                  double tol) {
     // delta is in units of eps
     const double scale = potmax + eps;
     const double tol_pot = std::max(tol, 1e-6) * scale;
-    if (delta * eps <= 4e-7 * scale) return true;  // rounding level
     if (!(delta_prev > 0.0) || m <= 0) return false;
+    // progress = a new smallest step (by at least 1 %) since the last check
+    if (delta < 0.99 * delta_best) {
+        delta_best = delta;
+        no_progress = 0;
+    } else {
+        ++no_progress;
+    }
     const double r = std::pow(delta / delta_prev, 1.0 / m);
-    if (!(r < 1.0)) return false;
-    return delta * eps * r / (1.0 - r) <= tol_pot;
+    if (r < 0.999 && delta * eps * r / (1.0 - r) <= tol_pot) return true;  // geometric tail
+    // three windows without a new smallest step: the float32 rounding floor of
+    // the duals; accept when the step itself is small
+    return no_progress >= 3 && delta * eps <= 1e-5 * scale;
 }
 
 int Solver::iterate_at_blur(const otgb_params &P, int it_budget) {
@@ -289,6 +354,10 @@ int Solver::iterate_at_blur(const otgb_params &P, int it_budget) {
     const int every = std::max(1, std::min(P.check_every, kEvPool));
     int at_blur = 0;
     double delta_prev = -1.0;
+    if (P.anderson > 0) {
+        aa.init(*ws, tag, 2 * X.n + 2 * Y.n, P.anderson, st);
+        aa_active = true;
+    }
     for (;;) {
         int m = 0;
         for (int k = 0; k < every && steps < P.max_iters; ++k, ++at_blur, ++m) fine_step(P.blur);
@@ -298,6 +367,9 @@ int Solver::iterate_at_blur(const otgb_params &P, int it_budget) {
         double rem = 0.0;
         const bool ok_s = converged(hist, P.tol, 1e-12 * eps * (X.mass + Y.mass), &rem);
         const bool ok_p = potentials_converged(delta_prev, last_delta, m, eps, last_potmax, P.tol);
+        if (trace_enabled())
+            std::fprintf(stderr, "otgb: step %d S %.12g rem %.3g delta %.3g potmax %.4g ok_s %d ok_p %d\n", steps, S,
+                         rem, last_delta, last_potmax, (int)ok_s, (int)ok_p);
         delta_prev = last_delta;
         last_rel = rem;
         if (ok_s && ok_p && at_blur >= P.min_iters) return OTGB_OK;
@@ -310,6 +382,11 @@ void Solver::fine_step(double sigma) {
     if (ms) ms->before_fine_step(*this, sigma);
     step(sigma, true);
     ++fine_steps;
+    if (translation && !std::isinf(rho)) {
+        double2 *part = ws->get<double2>(nm("tpart"), 64);
+        translate_duals(X.w, pf[cur], X.n, Y.w, pg[cur], Y.n, rho, part, nullptr, st);
+    }
+    if (aa_active) aa.step(Z[cur ^ 1], Z[cur], st);
 }
 
 }  // namespace otgb
@@ -345,6 +422,7 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         s.reach = P.reach;
         s.rho = (!(P.reach > 0.0) || std::isinf(P.reach)) ? INFINITY : P.reach * P.reach;
         s.timing = stats != nullptr;
+        s.translation = P.translation != 0;
         cudaStream_t st = s.st;
         OTGB_CUDA_TRY(cudaEventRecord(ctx_event(ctx, 0), st));
 
@@ -407,15 +485,12 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         s.alloc_pots(P);
 
         // rows per CTA: enough CTAs to fill the GPU twice, else the smallest blocks
-        const int sms = ctx_sm_count(ctx);
+        // rows per thread (D <= 3): dense blocks take 4 (one 128-thread CTA covers
+        // 512 rows; columns are split across CTAs); multiscale blocks take 2, a
+        // compromise between the reuse of each staged column (more rows) and a
+        // tight truncation (the block's kept set is the union over its clusters)
         s.rows_per_thread = 1;
-        if (D <= 3) {
-            for (int R : {4, 2}) {
-                const int br = 128 * R;
-                const long nb = 2L * ((N + br - 1) / br) + 2L * ((M + br - 1) / br);
-                if (nb >= 2L * sms) { s.rows_per_thread = R; break; }
-            }
-        }
+        if (D <= 3) s.rows_per_thread = P.multiscale ? 2 : 4;
         const int block_rows = D <= 3 ? 128 * s.rows_per_thread : 128;
         s.block_rows = block_rows;
 
@@ -539,10 +614,10 @@ extern "C" int otgb_softmin(otgb_ctx *ctx, const float *q, int n_out, const floa
         const int block_rows = 128 * rpt;
         int *blk = ws.get<int>("sm:blk", n_out / block_rows + 2);
         const int nb = uniform_blocks(blk, n_out, block_rows, st);
-        std::vector<int2> items(nb);
-        for (int k = 0; k < nb; ++k) items[k] = make_int2(0, k);
-        int2 *d_items = ws.get<int2>("sm:items", nb);
-        OTGB_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), nb * sizeof(int2), cudaMemcpyHostToDevice, st));
+        std::vector<int4> items(nb);
+        for (int k = 0; k < nb; ++k) items[k] = make_int4(0, k, 0, n_in);
+        int4 *d_items = ws.get<int4>("sm:items", nb);
+        OTGB_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), nb * sizeof(int4), cudaMemcpyHostToDevice, st));
         SoftminLaunch L;
         std::memset(&L, 0, sizeof(L));
         L.n_inst = 1;
@@ -552,6 +627,7 @@ extern "C" int otgb_softmin(otgb_ctx *ctx, const float *q, int n_out, const floa
         I.blk_row0 = blk;
         L.items = d_items;
         L.n_items = nb;
+        L.exact_max = 1;  // `old` is a blend target here, not an estimate of the result
         L.eps = (float)eps;
         L.s = (float)(1.4426950408889634 / eps);
         L.eps_ln2 = eps * 0.69314718055994530942;
@@ -560,7 +636,7 @@ extern "C" int otgb_softmin(otgb_ctx *ctx, const float *q, int n_out, const floa
         L.n_fallback = ws.get<int>("sm:nfb", 1);
         L.fallback_cap = cap;
         softmin_run(L, D, rpt, st);
-        OTGB_CUDA_TRY(cudaStreamSynchronize(st));
+        OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // the host item vector is released here
         return OTGB_OK;
     } catch (const Error &e) {
         return fail(ctx, e);

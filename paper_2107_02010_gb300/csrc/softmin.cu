@@ -103,25 +103,14 @@ constexpr int kT3 = 128;
 
 __device__ __forceinline__ bool row_sum_ok(float a) { return a >= 0x1p-60f && a <= 0x1p60f; }
 
+// Rows of a block in registers: thread t owns rows r0 + t + k 128, k < R,
+// translated by the centre of the block's bounding box; m = per-row shift from
+// the old values (EST) or 0 (TWO: filled later by the maximum pass).
 template <int R, bool TWO>
-__global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ SoftminLaunch L) {
-    __shared__ __align__(16) float4 tile[2][kT3][2];
-    __shared__ float red[kNT3 / 32];
-
-    int2 item = L.items[blockIdx.x];
-    OTGB_DCLAMP(item.x, 0, L.n_inst);
-    const SoftminInst &I = L.inst[item.x];
-    const int blk = item.y;
-    int r0 = I.blk_row0[blk], r1 = I.blk_row0[blk + 1];
-    OTGB_DCLAMP(r0, 0, I.n_rows + 1);
-    OTGB_DCLAMP(r1, r0, I.n_rows + 1);
+__device__ __forceinline__ void setup_rows3(const SoftminLaunch &L, const SoftminInst &I, int r0, int r1,
+                                            float *red, float (&xr)[R][3], float (&m)[R], float (&c)[3]) {
     const int t = threadIdx.x;
     const float4 *rows4 = reinterpret_cast<const float4 *>(I.rows);
-    const float4 *cols4 = reinterpret_cast<const float4 *>(I.cols);
-    const float eps = L.eps, s = L.s;
-
-    // rows and the centre of their bounding box
-    float xr[R][3];
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
 #pragma unroll
     for (int k = 0; k < R; ++k) {
@@ -135,14 +124,13 @@ __global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ 
         }
         xr[k][0] = p.x; xr[k][1] = p.y; xr[k][2] = p.z;
     }
-    float c[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const float l = block_min<kNT3>(lo[d], red);
         const float h = block_max<kNT3>(hi[d], red);
         c[d] = 0.5f * (l + h);
     }
-    float m[R];
+    const float s = L.s;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int r = r0 + t + k * kNT3;
@@ -155,19 +143,65 @@ __global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ 
             m[k] = (float)((double)s * (hx - (double)I.row_old[r] / (double)I.lam));
         }
     }
+}
 
-    // columns of this block
+// Finish the R rows of thread t from their sums: flag, log, blend, write.
+template <int R>
+__device__ __forceinline__ void finish_rows3(const SoftminLaunch &L, const SoftminInst &I, int inst, int blk, int r0,
+                                             int r1, const float (&xr)[R][3], const float (&m)[R],
+                                             const float (&tot)[R], float *red) {
+    float dmax = 0.f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int r = r0 + threadIdx.x + k * kNT3;
+        if (r >= r1) continue;
+        const float a = tot[k];
+        if (!row_sum_ok(a)) {
+            push_fallback(L, inst, r, blk);
+            continue;
+        }
+        const double hx = 0.5 * ((double)xr[k][0] * xr[k][0] + (double)xr[k][1] * xr[k][1] +
+                                 (double)xr[k][2] * xr[k][2]);
+        finish_row(L, I, r, (double)m[k] + log2((double)a), hx, dmax);
+    }
+    dmax = block_max<kNT3>(dmax, red);
+    if (threadIdx.x == 0 && L.delta_max) atomicMax(L.delta_max, __float_as_uint(dmax));
+}
+
+template <int R, bool TWO>
+__global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ SoftminLaunch L) {
+    __shared__ __align__(16) float4 tile[2][kT3][2];
+    __shared__ float red[kNT3 / 32];
+
+    int4 item = L.items[blockIdx.x];
+    OTGB_DCLAMP(item.x, 0, L.n_inst);
+    const SoftminInst &I = L.inst[item.x];
+    const int blk = item.y;
+    int r0 = I.blk_row0[blk], r1 = I.blk_row0[blk + 1];
+    OTGB_DCLAMP(r0, 0, I.n_rows + 1);
+    OTGB_DCLAMP(r1, r0, min(I.n_rows, r0 + R * kNT3) + 1);
+    const int t = threadIdx.x;
+    const float4 *cols4 = reinterpret_cast<const float4 *>(I.cols);
+    const float eps = L.eps, s = L.s;
+
+    float xr[R][3], m[R], c[3];
+    setup_rows3<R, TWO>(L, I, r0, r1, red, xr, m, c);
+
+    // this item's columns: positions [cb, ce) of the block's column sequence
     const int *list = I.col_list;
     int c0 = 0, c1 = I.n_cols;
     if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
-    const int ncol = c1 - c0;
+    int cb = item.z, ce = item.w;
+    OTGB_DCLAMP(cb, 0, c1 - c0 + 1);
+    OTGB_DCLAMP(ce, cb, c1 - c0 + 1);
+    const int ncol = ce - cb;
     const int ntiles = (ncol + kT3 - 1) / kT3;
 
-    // staging of one tile: thread t loads column p0 + t
+    // staging of one tile: thread t loads column p0 + t of this item
     auto load_col = [&](int p0, float4 &q, float &pot) {
         const int p = p0 + t;
         if (p < ncol) {
-            int j = list ? list[c0 + p] : p;
+            int j = list ? list[c0 + cb + p] : cb + p;
             OTGB_DCLAMP(j, 0, I.n_cols);
             q = cols4[j];
             pot = I.col_pot[j];
@@ -241,9 +275,10 @@ __global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ 
         int n = min(kT3, ncol - tt * kT3);
         n = (n + 3) & ~3;  // padded columns carry H = -inf
         if constexpr (R >= 2) {
-            u64 acc[P];
+            // two accumulators per row pair (even / odd columns) shorten the add chain
+            u64 acc[P][2];
 #pragma unroll
-            for (int p = 0; p < P; ++p) acc[p] = 0ull;
+            for (int p = 0; p < P; ++p) acc[p][0] = acc[p][1] = 0ull;
             const ulonglong2 *tp = reinterpret_cast<const ulonglong2 *>(&tile[buf][0][0]);
 #pragma unroll 4
             for (int cc = 0; cc < n; ++cc) {
@@ -256,52 +291,73 @@ __global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ 
                     v = fma2(X0[p], a.x, v);
                     float vl, vh;
                     unpack2(v, vl, vh);
-                    acc[p] = add2(acc[p], pack2(ex2(vl), ex2(vh)));
+                    acc[p][cc & 1] = add2(acc[p][cc & 1], pack2(ex2(vl), ex2(vh)));
                 }
             }
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                float al, ah;
-                unpack2(acc[p], al, ah);
-                tot[2 * p] += al;
-                tot[2 * p + 1] += ah;
+                float al, ah, bl, bh;
+                unpack2(acc[p][0], al, ah);
+                unpack2(acc[p][1], bl, bh);
+                tot[2 * p] += al + bl;
+                tot[2 * p + 1] += ah + bh;
             }
         } else {
-            float acc = 0.f;
+            float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll 4
-            for (int cc = 0; cc < n; ++cc) {
+            for (int cc = 0; cc < n; cc += 2) {
                 const float4 a = tile[buf][cc][0], b = tile[buf][cc][1];
                 float v = fmaf(xr[0][2], b.x, b.z - m[0]);
                 v = fmaf(xr[0][1], a.z, v);
                 v = fmaf(xr[0][0], a.x, v);
-                acc += ex2(v);
+                acc0 += ex2(v);
+                const float4 a2 = tile[buf][cc + 1][0], b2 = tile[buf][cc + 1][1];
+                float w = fmaf(xr[0][2], b2.x, b2.z - m[0]);
+                w = fmaf(xr[0][1], a2.z, w);
+                w = fmaf(xr[0][0], a2.x, w);
+                acc1 += ex2(w);
             }
-            tot[0] += acc;
+            tot[0] += acc0 + acc1;
         }
         if (more) store_col(buf ^ 1, q, pot);
         __syncthreads();
     }
 
-    // per-row finish
-    float dmax = 0.f;
+    if (t == 0 && L.pairs) atomicAdd(L.pairs, (unsigned long long)(r1 - r0) * (unsigned long long)ncol);
+    if (L.part) {
+        // split block: partial sums, finished by softmin3_finalize_kernel
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const int r = r0 + t + k * kNT3;
-        if (r >= r1) continue;
-        const float a = tot[k];
-        if (!row_sum_ok(a)) {
-            push_fallback(L, item.x, r, blk);
-            continue;
-        }
-        const double hx = 0.5 * ((double)xr[k][0] * xr[k][0] + (double)xr[k][1] * xr[k][1] +
-                                 (double)xr[k][2] * xr[k][2]);
-        finish_row(L, I, r, (double)m[k] + log2((double)a), hx, dmax);
+        for (int k = 0; k < R; ++k) L.part[(size_t)blockIdx.x * kPartRows + t + k * kNT3] = tot[k];
+        return;
     }
-    dmax = block_max<kNT3>(dmax, red);
-    if (t == 0) {
-        if (L.delta_max) atomicMax(L.delta_max, __float_as_uint(dmax));
-        if (L.pairs) atomicAdd(L.pairs, (unsigned long long)(r1 - r0) * (unsigned long long)ncol);
+    finish_rows3<R>(L, I, item.x, blk, r0, r1, xr, m, tot, red);
+}
+
+// Split blocks: one CTA per block sums the partial sums of its items in item
+// order (deterministic) and finishes the rows.  Only the EST shift is used
+// with splitting.
+template <int R>
+__global__ void __launch_bounds__(kNT3) softmin3_finalize_kernel(const __grid_constant__ SoftminLaunch L) {
+    __shared__ float red[kNT3 / 32];
+    int4 fe = L.fin[blockIdx.x];
+    OTGB_DCLAMP(fe.x, 0, L.n_inst);
+    const SoftminInst &I = L.inst[fe.x];
+    const int blk = fe.y;
+    int r0 = I.blk_row0[blk], r1 = I.blk_row0[blk + 1];
+    OTGB_DCLAMP(r0, 0, I.n_rows + 1);
+    OTGB_DCLAMP(r1, r0, min(I.n_rows, r0 + R * kNT3) + 1);
+    float xr[R][3], m[R], c[3];
+    setup_rows3<R, false>(L, I, r0, r1, red, xr, m, c);
+    float tot[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) tot[k] = 0.f;
+    for (int it = 0; it < fe.w; ++it) {
+        int item = fe.z + it;
+        OTGB_DCLAMP(item, 0, L.n_items);
+#pragma unroll
+        for (int k = 0; k < R; ++k) tot[k] += L.part[(size_t)item * kPartRows + threadIdx.x + k * kNT3];
     }
+    finish_rows3<R>(L, I, fe.x, blk, r0, r1, xr, m, tot, red);
 }
 
 // ------------------------------------------------------------ 3 < D <= 64 --
@@ -328,7 +384,7 @@ template <bool TWO>
 __global__ void __launch_bounds__(kNTg) softmin_gen_kernel(const __grid_constant__ SoftminLaunch L, int D, int D4) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GenSmem &S = *reinterpret_cast<GenSmem *>(smem_raw);
-    int2 item = L.items[blockIdx.x];
+    int4 item = L.items[blockIdx.x];
     OTGB_DCLAMP(item.x, 0, L.n_inst);
     const SoftminInst &I = L.inst[item.x];
     const int blk = item.y;
@@ -374,7 +430,11 @@ __global__ void __launch_bounds__(kNTg) softmin_gen_kernel(const __grid_constant
     const int *list = I.col_list;
     int c0 = 0, c1 = I.n_cols;
     if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
-    const int ncol = c1 - c0;
+    int cb = item.z, ce = item.w;
+    OTGB_DCLAMP(cb, 0, c1 - c0 + 1);
+    OTGB_DCLAMP(ce, cb, c1 - c0 + 1);
+    c0 += cb;  // this item sees positions [cb, ce) of the block's columns (never split for D > 3)
+    const int ncol = ce - cb;
     const int tr = t >> 4, tc = t & 15;
     const int ntiles = (ncol + kBN - 1) / kBN;
     const int D44 = D4 >> 2;
@@ -559,8 +619,10 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
     if (L.n_items <= 0) return;
     OTGB_CUDA_TRY(cudaMemsetAsync(L.n_fallback, 0, sizeof(int), st));
     // the first-pass maximum is needed when some instance has no old value
-    bool two = false;
+    bool two = L.exact_max != 0;
     for (int k = 0; k < L.n_inst; ++k) two = two || (L.inst[k].row_old == nullptr);
+    require(!(two && L.part), "softmin_run: split blocks need old values", OTGB_EINTERNAL);
+    require(!(D > 3 && L.part), "softmin_run: split blocks are D <= 3 only", OTGB_EINTERNAL);
     if (D <= 3) {
         switch (rows_per_thread + (two ? 8 : 0)) {
             case 1: softmin3_kernel<1, false><<<L.n_items, kNT3, 0, st>>>(L); break;
@@ -569,6 +631,15 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
             case 9: softmin3_kernel<1, true><<<L.n_items, kNT3, 0, st>>>(L); break;
             case 10: softmin3_kernel<2, true><<<L.n_items, kNT3, 0, st>>>(L); break;
             default: softmin3_kernel<4, true><<<L.n_items, kNT3, 0, st>>>(L); break;
+        }
+        OTGB_CHECK_LAUNCH();
+        if (L.part && L.n_fin > 0) {
+            switch (rows_per_thread) {
+                case 1: softmin3_finalize_kernel<1><<<L.n_fin, kNT3, 0, st>>>(L); break;
+                case 2: softmin3_finalize_kernel<2><<<L.n_fin, kNT3, 0, st>>>(L); break;
+                default: softmin3_finalize_kernel<4><<<L.n_fin, kNT3, 0, st>>>(L); break;
+            }
+            OTGB_CHECK_LAUNCH();
         }
     } else {
         const int D4 = (D + 3) & ~3;
@@ -582,8 +653,8 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
         }
         if (two) softmin_gen_kernel<true><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
         else softmin_gen_kernel<false><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
+        OTGB_CHECK_LAUNCH();
     }
-    OTGB_CHECK_LAUNCH();
     const int stride = D <= 3 ? 4 : ((D + 3) & ~3);
     softmin_fallback_kernel<<<64, 256, 0, st>>>(L, D, stride);
     OTGB_CHECK_LAUNCH();

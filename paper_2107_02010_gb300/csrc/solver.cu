@@ -111,6 +111,8 @@ void otgb_default_params(otgb_params *p) {
     p->fixed_iters = 0;
     p->precision = OTGB_FP32;
     p->sigma_start = 0.0;
+    p->translation = 1;
+    p->anderson = 5;
 }
 
 int otgb_create(otgb_ctx **out, int device, void *cuda_stream) {

@@ -44,6 +44,8 @@ class Params(C.Structure):
         ("a_init", C.c_void_p),
         ("b_init", C.c_void_p),
         ("sigma_start", C.c_double),
+        ("translation", C.c_int),
+        ("anderson", C.c_int),
     ]
 
 

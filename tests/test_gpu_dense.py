@@ -135,7 +135,8 @@ def _run_pair(ctx, x, a, y, b, blur, reach, q, extra):
 
     d = oracle.diameter(x, y)
     n_sched = len(oracle.schedule(d, blur, q))
-    p = otgb.default_params(blur=blur, reach=reach, scaling=q, diameter=d, fixed_iters=extra)
+    # the paper's loop step for step (no translation step), as the oracle runs it
+    p = otgb.default_params(blur=blur, reach=reach, scaling=q, diameter=d, fixed_iters=extra, translation=0)
     out = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b), p, want_self=True)
     ref = oracle.sinkhorn(x, a, y, b, blur=blur, reach=reach, scaling=q, diameter=d, tol=0.0,
                           max_iters=n_sched + extra)
@@ -199,6 +200,29 @@ def test_converged_solve_matches_converged_oracle(ctx):
     eps = blur ** 2
     assert abs(out["S"] - ref["S"]) <= TOL * abs(ref["S"]), (out["S"], ref["S"])
     check_pots(out, ref, a, b, eps, reach)
+
+
+@pytest.mark.parametrize("translation,anderson", [(0, 0), (1, 0), (0, 5), (1, 5)])
+def test_accelerations_keep_the_fixed_point(ctx, translation, anderson):
+    # unbalanced, slow (lambda close to 1): the translation step and Anderson
+    # mixing change the number of steps, not the converged result.  The plain
+    # averaged loop (0, 0) cannot resolve its slowest mode below the float32
+    # step noise, so only S is required of it.
+    from paper_2107_02010_gb300 import otgb
+
+    x, a, y, b = synth.rotated_cloud(300, 250, seed=21)
+    b = (b * 1.3).astype(np.float32)
+    blur, reach = 0.1, 0.5
+    ref = oracle.sinkhorn(x, a, y, b, blur=blur, reach=reach, scaling=0.5, tol=1e-12, max_iters=100000)
+    assert ref["converged"]
+    p = otgb.default_params(blur=blur, reach=reach, scaling=0.5, tol=1e-8, max_iters=50000,
+                            translation=translation, anderson=anderson)
+    out = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b), p, want_self=True)
+    print("translation", translation, "anderson", anderson, "steps", out["stats"]["iters_total"],
+          "oracle steps", ref["iters"])
+    assert abs(out["S"] - ref["S"]) <= TOL * abs(ref["S"]), (out["S"], ref["S"])
+    if translation or anderson:
+        check_pots(out, ref, a, b, blur ** 2, reach)
 
 
 def test_self_divergence_is_zero_on_gpu(ctx):

@@ -198,6 +198,24 @@ def test_dual_form_eq6_equals_definition_eq5(reach):
     assert r["S"] == pytest.approx(S5, rel=1e-10, abs=1e-14)
 
 
+def test_unbalanced_plan_masses_agree_at_the_fixed_point():
+    # At the unbalanced fixed point sum_j b_j exp((f_i + g_j - C_ij)/eps) = e^{-f_i/rho}
+    # (damped softmin), so the plan mass is <alpha, e^{-f/rho}> = <beta, e^{-g/rho}>:
+    # the translation (f + c, g - c) with c = (rho/2) log of their ratio is 0 there.
+    x, y = _cloud(30, seed=27), _cloud(22, seed=28)
+    a, b = _weights(30, seed=29), _weights(22, seed=30, total=1.4)
+    blur, reach = 0.2, 0.7
+    r = oracle.sinkhorn(x, a, y, b, blur=blur, reach=reach, scaling=0.5)
+    rho = oracle.rho(reach)
+    A = float(a.astype(np.float64) @ np.exp(-r["f"] / rho))
+    B = float(b.astype(np.float64) @ np.exp(-r["g"] / rho))
+    assert A == pytest.approx(B, rel=1e-11)
+    eps = blur ** 2
+    C = 0.5 * ((x[:, None].astype(np.float64) - y[None]) ** 2).sum(-1)
+    plan = a[:, None].astype(np.float64) * b[None] * np.exp((r["f"][:, None] + r["g"][None] - C) / eps)
+    assert plan.sum() == pytest.approx(A, rel=1e-10)
+
+
 def test_fixed_point_of_plain_update():
     # At convergence each vector is a fixed point of its own (undamped-average)
     # softmin update of the Algorithm, Section 2.
