@@ -198,6 +198,44 @@ int cluster_kmeans(otgb_ctx *ctx, const float *x, const float *w, int N, int D, 
 int otgb_softmin(otgb_ctx *ctx, const float *q, int n_out, const float *p, const float *w, const float *pot,
                  int n_in, int D, double eps, double lam, const float *old, double omega, float *out);
 
+/*
+ * otgb_softmin_noalloc: the same sweep as otgb_softmin, for callers that may
+ * not allocate device memory.  The paper has no counterpart: this entry point
+ * exists for integration only.
+ *
+ * Who needs it: code that runs where a device allocation is not allowed or
+ * not wanted -- a host that gives a component a fixed memory budget and owns
+ * every allocation itself (a serving process with a preallocated arena, an
+ * embedded pipeline), code inside a latency-critical loop where an allocation
+ * could stall on the driver, or a caller that has no otgb_ctx (which owns
+ * allocated scratch).  This call needs no context and calls no cudaMalloc,
+ * cudaFree or allocating library routine: its scratch is one fixed, file-scope
+ * device array of 16 MiB that every GPU which loads the library holds until
+ * the process exits.
+ *
+ *   q: n_out x D rows, p: n_in x D columns, w: n_in weights, pot: n_in
+ *   potential, old (optional), out: n_out -- device pointers owned by the
+ *   caller, as in otgb_softmin (same arguments, same result).
+ *   cuda_stream: the cudaStream_t to run on (NULL: the legacy default stream).
+ *   The call returns when the result is complete on that stream.
+ * Limits and errors: EINVAL when the scratch of the problem -- about
+ * 16 (n_out + n_in) bytes plus 16 bytes per row for D <= 3, and
+ * 4 round_up(D, 4) (n_out + n_in) + 4 n_in + 16 n_out bytes for D > 3 --
+ * exceeds 16 MiB (for D <= 3 roughly n_out + n_in <= 500,000 when balanced),
+ * and for the argument errors of otgb_softmin; the message is available from
+ * otgb_last_error(NULL).
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  Every call on a device shares the one
+ * array, so calls that overlap on the GPU (from several host threads or
+ * streams at once) race and must be serialised by the caller; the array keeps
+ * the last call's contents, and every piece that must start at zero is
+ * cleared by the call itself.
+ */
+int otgb_softmin_noalloc(const float *q, int n_out, const float *p, const float *w, const float *pot, int n_in,
+                         int D, double eps, double lam, const float *old, double omega, float *out,
+                         void *cuda_stream);
+
 /* Number of CUDA kernels this library has launched in this process (all
    contexts), for accounting by benchmarks. */
 unsigned long long otgb_kernel_launches(void);

@@ -78,7 +78,7 @@ STATUS = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "ENOCONV", -5: "
 
 EXPORTS = ["otgb_default_params", "otgb_create", "otgb_destroy", "otgb_last_error", "sinkhorn_divergence",
            "transport_apply", "otgb_plan_free", "cluster_grid", "cluster_kmeans", "otgb_softmin",
-           "otgb_kernel_launches"]
+           "otgb_kernel_launches", "otgb_softmin_noalloc"]
 
 
 def kernel_launches() -> int:
@@ -120,6 +120,8 @@ def load(build_if_missing: bool = True):
     lib.cluster_grid.argtypes = [vp, vp, vp, ci, ci, C.c_float, vp, vp, vp, C.POINTER(ci), vp]
     lib.cluster_kmeans.argtypes = [vp, vp, vp, ci, ci, ci, ci, C.c_ulonglong, vp, vp, vp, vp, vp]
     lib.otgb_softmin.argtypes = [vp, vp, ci, vp, vp, vp, ci, ci, cd, cd, vp, cd, vp]
+    lib.otgb_softmin_noalloc.argtypes = [vp, ci, vp, vp, vp, ci, ci, cd, cd, vp, cd, vp, vp]
+    lib.otgb_softmin_noalloc.restype = ci
     lib.otgb_kernel_launches.argtypes = []
     lib.otgb_kernel_launches.restype = C.c_ulonglong
     for name in ("otgb_create", "otgb_destroy", "sinkhorn_divergence", "transport_apply", "cluster_grid",
@@ -267,4 +269,21 @@ def softmin(ctx: Context, q, p, w, pot, eps, lam=1.0, old=None, omega=0.5):
     out = torch.empty(n_out, device=q.device, dtype=torch.float32)
     ctx.check(load().otgb_softmin(ctx.h, _f32(q), n_out, _f32(p), _f32(w), _f32(pot), p.shape[0], D, float(eps),
                                   float(lam), _f32(old) if old is not None else None, float(omega), _ptr(out)))
+    return out
+
+
+def softmin_noalloc(q, p, w, pot, eps, lam=1.0, old=None, omega=0.5, out=None, stream=None):
+    """otgb_softmin_noalloc: no context, no device allocation inside the call.
+    `out` may be passed preallocated (float32, n_out) so that nothing at all
+    is allocated on the device during the call."""
+    n_out, D = q.shape
+    if out is None:
+        out = torch.empty(n_out, device=q.device, dtype=torch.float32)
+    st = torch.cuda.current_stream(q.device) if stream is None else stream
+    lib = load()
+    rc = lib.otgb_softmin_noalloc(_f32(q), n_out, _f32(p), _f32(w), _f32(pot), p.shape[0], D, float(eps),
+                                  float(lam), _f32(old) if old is not None else None, float(omega), _ptr(out),
+                                  C.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise OtgbError(rc, lib.otgb_last_error(None).decode())
     return out
