@@ -27,7 +27,9 @@ sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # Measured per-SM, per-clock rates on GB300 (sm_103a): ex2.approx 32/clk,
-# FP32 FMA 128 lanes/clk (f32x2 packing halves issue, not FP32 work).
+# FP32 FMA 128 lanes/clk (f32x2 packing halves issue, not FP32 work).  A pair of
+# a stable log-sum-exp in the dot-product form costs D FMAs, one add (the row's
+# reference), one add (accumulate) and one ex2.
 SFU_EX2_PER_CLK_SM = 32
 FP32_LANES_PER_CLK_SM = 128
 
@@ -111,7 +113,7 @@ def cpu_baseline(x, a, y, b, rows=2048):
 
 
 def peak_pairs_per_s(D, clock_mhz, n_sm):
-    per_clk = min(SFU_EX2_PER_CLK_SM, FP32_LANES_PER_CLK_SM / (D + 1))
+    per_clk = min(SFU_EX2_PER_CLK_SM, FP32_LANES_PER_CLK_SM / (D + 2))
     return per_clk * n_sm * clock_mhz * 1e6
 
 
@@ -270,7 +272,7 @@ def main():
         "roofline": {"bound": "alu", "kernel": "softmin3_kernel (+ fallback, per softmin launch)",
                      "achieved": achieved / 1e9 if achieved else None, "peak": peak / 1e9, "unit": "Gpairs/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "peak_basis": "%d SMs x min(32 ex2, 128/(D+1) FP32) pairs/clk x %.0f MHz (measured per-clock "
+                     "peak_basis": "%d SMs x min(32 ex2, 128/(D+2) FP32) pairs/clk x %.0f MHz (measured per-clock "
                                    "rates; clock = sm_max_mhz of MEASURED_PEAKS.json)" % (n_sm, clk)},
         "e2e": {"value": e2e_val, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
