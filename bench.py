@@ -43,7 +43,8 @@ def workload(args):
 
 def params_for(args, otgb):
     return otgb.default_params(blur=1.0, reach=10.0, scaling=0.5, multiscale=int(args.multiscale), cluster=0,
-                               cell=4.0, tol=args.tol, max_iters=args.max_iters, check_every=10)
+                               cell=4.0, tol=args.tol, max_iters=args.max_iters, check_every=10,
+                               rows_per_thread=args.rows_per_thread)
 
 
 def start_clock_sampler():
@@ -155,6 +156,7 @@ def main():
     ap.add_argument("--max-iters", type=int, default=20000)
     ap.add_argument("--ref-rows", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows-per-thread", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

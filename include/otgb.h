@@ -80,6 +80,8 @@ typedef struct {
     int anderson;          /* > 0: Anderson acceleration with this history length (<= 8) of the steps at
                               sigma = blur (Walker & Ni 2011); the fixed point is unchanged.  0: off.
                               Default 5. */
+    int rows_per_thread;   /* D <= 3 kernel tuning: rows per thread (1, 2 or 4; a block holds 128 x this many
+                              rows); 0 = automatic (4 dense, 2 multiscale). */
 } otgb_params;
 
 /* Statistics of one solve (host struct, filled when non-null). */
@@ -150,7 +152,7 @@ int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a, int N, co
  *   scores: N x L float32 (optional), argmax: N int32 (lowest class on ties;
  *     -1 when the row is empty), row_mass: N float32 = sum_l Lab_il (optional).
  * A row whose mass is near 0 is an outlier (Section 2, label transfer).
- * Truncated plans reuse the cluster-pair mask of the last fine step.
+ * The sum runs over all atlas points (dense), for any 1 <= D <= 64.
  * Errors: EINVAL for a null plan, L < 1 or L > 1024, null f/g/labels/argmax.
  */
 int transport_apply(otgb_ctx *ctx, const otgb_plan *plan, const float *f, const float *g, const int32_t *labels,

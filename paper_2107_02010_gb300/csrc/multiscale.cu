@@ -342,8 +342,8 @@ int Multiscale::run_schedule(Solver &s, const otgb_params &P, const std::vector<
         otgb_params Pc = P;
         Pc.f_init = Pc.g_init = Pc.a_init = Pc.b_init = nullptr;
         cs.alloc_pots(Pc);
-        cs.rows_per_thread = 1;
-        cs.setup_dense_instances(128);
+        cs.rows_per_thread = D <= 3 ? 4 : 1;
+        cs.setup_dense_instances(D <= 3 ? 32 * cs.rows_per_thread : 128);
         for (; k < sched.size() && sched[k] > sigma_switch && s.steps < P.max_iters; ++k) {
             cs.step(sched[k], false);
             ++s.steps;

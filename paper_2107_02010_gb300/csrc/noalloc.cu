@@ -76,8 +76,8 @@ extern "C" int otgb_softmin_noalloc(const float *q, int n_out, const float *p, c
         int rpt = 1;
         if (D <= 3)
             for (int r : {4, 2})
-                if ((n_out + 128 * r - 1) / (128 * r) >= 2 * sms) { rpt = r; break; }
-        const int block_rows = 128 * rpt;
+                if ((n_out + 32 * r - 1) / (32 * r) >= 8 * sms) { rpt = r; break; }
+        const int block_rows = D <= 3 ? 32 * rpt : 128;
         const int nb = (n_out + block_rows - 1) / block_rows;
         // scratch layout; the sizes decide admissibility
         Carve dry{nullptr};

@@ -113,14 +113,16 @@ struct SoftminInst {
 
 constexpr int kMaxInst = 4;
 
-// Work decomposition: one CTA per item (inst, blk, cb, ce) = the rows of
-// block blk of instance inst against the positions [cb, ce) of the block's
-// column sequence.  When a block's columns are split over several items, each
-// item writes its per-row partial sums (same per-row shift in every item) to
-// part[item * kPartRows + local row] and a finalize CTA per block, listed in
+// Work decomposition: one item (inst, blk, cb, ce) = the rows of block blk of
+// instance inst against the positions [cb, ce) of the block's column sequence;
+// the D <= 3 kernel runs one item per warp (blocks of at most 32 R = 128
+// rows), the high-dimensional kernel one item per CTA (128 rows).  When a
+// block's columns are split over several items, each item writes its per-row
+// partial sums (same per-row shift in every item) to
+// part[item * kPartRows + local row] and a finalize warp per block, listed in
 // fin as (inst, blk, first item, item count), sums them in a fixed order and
 // finishes the rows.  Only the D <= 3 kernel splits.
-constexpr int kPartRows = 512;
+constexpr int kPartRows = 128;
 
 struct SoftminLaunch {
     SoftminInst inst[kMaxInst];

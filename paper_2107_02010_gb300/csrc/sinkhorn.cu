@@ -211,15 +211,16 @@ void Solver::setup_dense_instances(int block_rows) {
 }
 
 // Items (inst, blk, cb, ce): a block's columns are cut into chunks of CH
-// positions, CH chosen so that the launch has about three waves of CTAs
-// (six resident per SM); every block of a split launch goes through the
-// finalize pass, which sums its items' partial sums in item order.
+// positions, CH chosen so that the launch has about three waves of items
+// (D <= 3: one item per warp, 6 CTAs of 4 warps resident per SM); every block
+// of a split launch goes through the finalize pass, which sums its items'
+// partial sums in item order.
 void Solver::set_work(const std::vector<std::vector<int>> &ncols, bool allow_split) {
     const int sms = ctx_sm_count(ctx);
     double W = 0.0;
     for (auto &v : ncols)
         for (int c : v) W += c;
-    const double target = 3.0 * 6.0 * sms;
+    const double target = 3.0 * 5.0 * 4.0 * sms;
     int CH = 1 << 30;
     if (allow_split) {
         CH = (int)std::ceil(W / target);
@@ -485,13 +486,14 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         s.alloc_pots(P);
 
         // rows per CTA: enough CTAs to fill the GPU twice, else the smallest blocks
-        // rows per thread (D <= 3): dense blocks take 4 (one 128-thread CTA covers
-        // 512 rows; columns are split across CTAs); multiscale blocks take 2, a
-        // compromise between the reuse of each staged column (more rows) and a
-        // tight truncation (the block's kept set is the union over its clusters)
+        // rows per thread (D <= 3): 4, so that one warp's block holds 128 rows
+        // (each staged column feeds 4 rows per lane, and the block's kept set --
+        // the union over its clusters -- stays small)
         s.rows_per_thread = 1;
-        if (D <= 3) s.rows_per_thread = P.multiscale ? 2 : 4;
-        const int block_rows = D <= 3 ? 128 * s.rows_per_thread : 128;
+        if (D <= 3) s.rows_per_thread = 4;
+        if (D <= 3 && (P.rows_per_thread == 1 || P.rows_per_thread == 2 || P.rows_per_thread == 4))
+            s.rows_per_thread = P.rows_per_thread;
+        const int block_rows = D <= 3 ? 32 * s.rows_per_thread : 128;
         s.block_rows = block_rows;
 
         std::vector<double> sched = make_schedule(diameter, P.blur, P.scaling);
@@ -609,9 +611,9 @@ extern "C" int otgb_softmin(otgb_ctx *ctx, const float *q, int n_out, const floa
         if (D <= 3) {
             const int sms = ctx_sm_count(ctx);
             for (int r : {4, 2})
-                if ((n_out + 128 * r - 1) / (128 * r) >= 2 * sms) { rpt = r; break; }
+                if ((n_out + 32 * r - 1) / (32 * r) >= 8 * sms) { rpt = r; break; }
         }
-        const int block_rows = 128 * rpt;
+        const int block_rows = D <= 3 ? 32 * rpt : 128;
         int *blk = ws.get<int>("sm:blk", n_out / block_rows + 2);
         const int nb = uniform_blocks(blk, n_out, block_rows, st);
         std::vector<int4> items(nb);

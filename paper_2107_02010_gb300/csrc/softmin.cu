@@ -94,27 +94,40 @@ __device__ __forceinline__ void push_fallback(const SoftminLaunch &L, int inst, 
 }
 
 // ------------------------------------------------------------ D <= 3 ------
-// 128 threads; each owns R rows (rows t, t+128, ...).  With R >= 2 the rows
-// go in pairs through packed f32x2 FMAs.  Columns are staged 128 per tile as
-// (Y0,Y0,Y1,Y1 | Y2,Y2,H,H) so that one 16-byte shared load feeds a packed
-// operand pair.  TWO = true: exact-maximum first pass (no old value).
-constexpr int kNT3 = 128;
-constexpr int kT3 = 128;
+// Warp-granular: a block is the 32 x R rows of ONE warp (lane l owns rows
+// r0 + l + 32 k, k < R), with its own column list; a CTA runs four independent
+// warps.  Blocks therefore stay small (tight truncation unions) while each
+// staged column still feeds R rows per lane, and no CTA barrier is needed.
+// With R >= 2 the rows go in pairs through packed f32x2 FMAs.  Each warp
+// stages 32 columns per tile as (Y0,Y0,Y1,Y1 | Y2,Y2,H,H), double buffered, so
+// that one 16-byte shared load feeds a packed operand pair.  TWO = true: an
+// exact-maximum first pass gives each row's shift (no old value).
+constexpr int kW3 = 4;    // warps per CTA
+constexpr int kT3 = 128;  // columns per warp tile (4 staged per lane)
+constexpr int kCPL = kT3 / 32;
 
 __device__ __forceinline__ bool row_sum_ok(float a) { return a >= 0x1p-60f && a <= 0x1p60f; }
 
-// Rows of a block in registers: thread t owns rows r0 + t + k 128, k < R,
-// translated by the centre of the block's bounding box; m = per-row shift from
-// the old values (EST) or 0 (TWO: filled later by the maximum pass).
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Rows of a warp block in registers, translated by the centre of their
+// bounding box; m = per-row shift from the old values (or 0 with TWO).
 template <int R, bool TWO>
 __device__ __forceinline__ void setup_rows3(const SoftminLaunch &L, const SoftminInst &I, int r0, int r1,
-                                            float *red, float (&xr)[R][3], float (&m)[R], float (&c)[3]) {
-    const int t = threadIdx.x;
+                                            float (&xr)[R][3], float (&m)[R], float (&c)[3]) {
+    const int lane = threadIdx.x & 31;
     const float4 *rows4 = reinterpret_cast<const float4 *>(I.rows);
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-        const int r = r0 + t + k * kNT3;
+        const int r = r0 + lane + 32 * k;
         float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
         if (r < r1) {
             p = rows4[r];
@@ -125,15 +138,11 @@ __device__ __forceinline__ void setup_rows3(const SoftminLaunch &L, const Softmi
         xr[k][0] = p.x; xr[k][1] = p.y; xr[k][2] = p.z;
     }
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const float l = block_min<kNT3>(lo[d], red);
-        const float h = block_max<kNT3>(hi[d], red);
-        c[d] = 0.5f * (l + h);
-    }
+    for (int d = 0; d < 3; ++d) c[d] = 0.5f * (warp_min(lo[d]) + warp_max(hi[d]));
     const float s = L.s;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-        const int r = r0 + t + k * kNT3;
+        const int r = r0 + lane + 32 * k;
 #pragma unroll
         for (int d = 0; d < 3; ++d) xr[k][d] = (r < r1) ? xr[k][d] - c[d] : 0.f;
         m[k] = 0.f;
@@ -145,15 +154,16 @@ __device__ __forceinline__ void setup_rows3(const SoftminLaunch &L, const Softmi
     }
 }
 
-// Finish the R rows of thread t from their sums: flag, log, blend, write.
+// Finish the R rows of this lane from their sums: flag, log, blend, write.
 template <int R>
 __device__ __forceinline__ void finish_rows3(const SoftminLaunch &L, const SoftminInst &I, int inst, int blk, int r0,
                                              int r1, const float (&xr)[R][3], const float (&m)[R],
-                                             const float (&tot)[R], float *red) {
+                                             const float (&tot)[R]) {
+    const int lane = threadIdx.x & 31;
     float dmax = 0.f;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-        const int r = r0 + threadIdx.x + k * kNT3;
+        const int r = r0 + lane + 32 * k;
         if (r >= r1) continue;
         const float a = tot[k];
         if (!row_sum_ok(a)) {
@@ -164,28 +174,30 @@ __device__ __forceinline__ void finish_rows3(const SoftminLaunch &L, const Softm
                                  (double)xr[k][2] * xr[k][2]);
         finish_row(L, I, r, (double)m[k] + log2((double)a), hx, dmax);
     }
-    dmax = block_max<kNT3>(dmax, red);
-    if (threadIdx.x == 0 && L.delta_max) atomicMax(L.delta_max, __float_as_uint(dmax));
+    dmax = warp_max(dmax);
+    if (lane == 0 && L.delta_max) atomicMax(L.delta_max, __float_as_uint(dmax));
 }
 
 template <int R, bool TWO>
-__global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ SoftminLaunch L) {
-    __shared__ __align__(16) float4 tile[2][kT3][2];
-    __shared__ float red[kNT3 / 32];
+__global__ void __launch_bounds__(32 * kW3, 5) softmin3_kernel(const __grid_constant__ SoftminLaunch L) {
+    __shared__ __align__(16) float4 tiles[kW3][2][kT3][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it = blockIdx.x * kW3 + warp;
+    if (it >= L.n_items) return;  // whole warp: no CTA-wide barrier follows
+    float4 (*tile)[kT3][2] = tiles[warp];
 
-    int4 item = L.items[blockIdx.x];
+    int4 item = L.items[it];
     OTGB_DCLAMP(item.x, 0, L.n_inst);
     const SoftminInst &I = L.inst[item.x];
     const int blk = item.y;
     int r0 = I.blk_row0[blk], r1 = I.blk_row0[blk + 1];
     OTGB_DCLAMP(r0, 0, I.n_rows + 1);
-    OTGB_DCLAMP(r1, r0, min(I.n_rows, r0 + R * kNT3) + 1);
-    const int t = threadIdx.x;
+    OTGB_DCLAMP(r1, r0, min(I.n_rows, r0 + 32 * R) + 1);
     const float4 *cols4 = reinterpret_cast<const float4 *>(I.cols);
     const float eps = L.eps, s = L.s;
 
     float xr[R][3], m[R], c[3];
-    setup_rows3<R, TWO>(L, I, r0, r1, red, xr, m, c);
+    setup_rows3<R, TWO>(L, I, r0, r1, xr, m, c);
 
     // this item's columns: positions [cb, ce) of the block's column sequence
     const int *list = I.col_list;
@@ -197,26 +209,32 @@ __global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ 
     const int ncol = ce - cb;
     const int ntiles = (ncol + kT3 - 1) / kT3;
 
-    // staging of one tile: thread t loads column p0 + t of this item
-    auto load_col = [&](int p0, float4 &q, float &pot) {
-        const int p = p0 + t;
-        if (p < ncol) {
-            int j = list ? list[c0 + cb + p] : cb + p;
-            OTGB_DCLAMP(j, 0, I.n_cols);
-            q = cols4[j];
-            pot = I.col_pot[j];
-        } else {
-            q = make_float4(0.f, 0.f, 0.f, -INFINITY);
-            pot = 0.f;
+    // staging of one tile: lane l loads columns p0 + l + 32 u, u < kCPL
+    auto load_col = [&](int p0, float4 (&q)[kCPL], float (&pot)[kCPL]) {
+#pragma unroll
+        for (int u = 0; u < kCPL; ++u) {
+            const int p = p0 + lane + 32 * u;
+            if (p < ncol) {
+                int j = list ? list[c0 + cb + p] : cb + p;
+                OTGB_DCLAMP(j, 0, I.n_cols);
+                q[u] = cols4[j];
+                pot[u] = I.col_pot[j];
+            } else {
+                q[u] = make_float4(0.f, 0.f, 0.f, -INFINITY);
+                pot[u] = 0.f;
+            }
         }
     };
-    auto store_col = [&](int buf, const float4 &q, float pot) {
-        const float y0 = q.x - c[0], y1 = q.y - c[1], y2 = q.z - c[2];
-        const float stuff = fmaf(eps, q.w, pot);
-        const float H = s * (stuff - 0.5f * (y0 * y0 + y1 * y1 + y2 * y2));
-        const float Y0 = s * y0, Y1 = s * y1, Y2 = s * y2;
-        tile[buf][t][0] = make_float4(Y0, Y0, Y1, Y1);
-        tile[buf][t][1] = make_float4(Y2, Y2, H, H);
+    auto store_col = [&](int buf, const float4 (&q)[kCPL], const float (&pot)[kCPL]) {
+#pragma unroll
+        for (int u = 0; u < kCPL; ++u) {
+            const float y0 = q[u].x - c[0], y1 = q[u].y - c[1], y2 = q[u].z - c[2];
+            const float stuff = fmaf(eps, q[u].w, pot[u]);
+            const float H = s * (stuff - 0.5f * (y0 * y0 + y1 * y1 + y2 * y2));
+            const float Y0 = s * y0, Y1 = s * y1, Y2 = s * y2;
+            tile[buf][lane + 32 * u][0] = make_float4(Y0, Y0, Y1, Y1);
+            tile[buf][lane + 32 * u][1] = make_float4(Y2, Y2, H, H);
+        }
     };
 
     constexpr int P = R / 2;  // packed row pairs
@@ -228,15 +246,15 @@ __global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ 
         X2[p] = pack2(xr[2 * p][2], xr[2 * p + 1][2]);
     }
 
-    float4 q;
-    float pot;
+    float4 q[kCPL];
+    float pot[kCPL];
     if constexpr (TWO) {
         // first pass: exact maximum of the exponents of each row
         float mx[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) mx[k] = -INFINITY;
         if (ntiles > 0) { load_col(0, q, pot); store_col(0, q, pot); }
-        __syncthreads();
+        __syncwarp();
         for (int tt = 0; tt < ntiles; ++tt) {
             const int buf = tt & 1;
             const bool more = tt + 1 < ntiles;
@@ -253,7 +271,7 @@ __global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ 
                 }
             }
             if (more) store_col(buf ^ 1, q, pot);
-            __syncthreads();
+            __syncwarp();
         }
 #pragma unroll
         for (int k = 0; k < R; ++k) m[k] = mx[k] > -INFINITY ? mx[k] : 0.f;
@@ -267,7 +285,7 @@ __global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ 
     for (int p = 0; p < P; ++p) Mn[p] = pack2(-m[2 * p], -m[2 * p + 1]);
 
     if (ntiles > 0) { load_col(0, q, pot); store_col(0, q, pot); }
-    __syncthreads();
+    __syncwarp();
     for (int tt = 0; tt < ntiles; ++tt) {
         const int buf = tt & 1;
         const bool more = tt + 1 < ntiles;
@@ -319,45 +337,48 @@ __global__ void __launch_bounds__(kNT3) softmin3_kernel(const __grid_constant__ 
             }
             tot[0] += acc0 + acc1;
         }
+        __syncwarp();  // every lane is done reading buf before it is refilled
         if (more) store_col(buf ^ 1, q, pot);
-        __syncthreads();
+        __syncwarp();
     }
 
-    if (t == 0 && L.pairs) atomicAdd(L.pairs, (unsigned long long)(r1 - r0) * (unsigned long long)ncol);
+    if (lane == 0 && L.pairs) atomicAdd(L.pairs, (unsigned long long)(r1 - r0) * (unsigned long long)ncol);
     if (L.part) {
         // split block: partial sums, finished by softmin3_finalize_kernel
 #pragma unroll
-        for (int k = 0; k < R; ++k) L.part[(size_t)blockIdx.x * kPartRows + t + k * kNT3] = tot[k];
+        for (int k = 0; k < R; ++k) L.part[(size_t)it * kPartRows + lane + 32 * k] = tot[k];
         return;
     }
-    finish_rows3<R>(L, I, item.x, blk, r0, r1, xr, m, tot, red);
+    finish_rows3<R>(L, I, item.x, blk, r0, r1, xr, m, tot);
 }
 
-// Split blocks: one CTA per block sums the partial sums of its items in item
+// Split blocks: one warp per block sums the partial sums of its items in item
 // order (deterministic) and finishes the rows.  Only the EST shift is used
 // with splitting.
 template <int R>
-__global__ void __launch_bounds__(kNT3) softmin3_finalize_kernel(const __grid_constant__ SoftminLaunch L) {
-    __shared__ float red[kNT3 / 32];
-    int4 fe = L.fin[blockIdx.x];
+__global__ void __launch_bounds__(32 * kW3) softmin3_finalize_kernel(const __grid_constant__ SoftminLaunch L) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int fi = blockIdx.x * kW3 + warp;
+    if (fi >= L.n_fin) return;
+    int4 fe = L.fin[fi];
     OTGB_DCLAMP(fe.x, 0, L.n_inst);
     const SoftminInst &I = L.inst[fe.x];
     const int blk = fe.y;
     int r0 = I.blk_row0[blk], r1 = I.blk_row0[blk + 1];
     OTGB_DCLAMP(r0, 0, I.n_rows + 1);
-    OTGB_DCLAMP(r1, r0, min(I.n_rows, r0 + R * kNT3) + 1);
+    OTGB_DCLAMP(r1, r0, min(I.n_rows, r0 + 32 * R) + 1);
     float xr[R][3], m[R], c[3];
-    setup_rows3<R, false>(L, I, r0, r1, red, xr, m, c);
+    setup_rows3<R, false>(L, I, r0, r1, xr, m, c);
     float tot[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) tot[k] = 0.f;
-    for (int it = 0; it < fe.w; ++it) {
-        int item = fe.z + it;
+    for (int q = 0; q < fe.w; ++q) {
+        int item = fe.z + q;
         OTGB_DCLAMP(item, 0, L.n_items);
 #pragma unroll
-        for (int k = 0; k < R; ++k) tot[k] += L.part[(size_t)item * kPartRows + threadIdx.x + k * kNT3];
+        for (int k = 0; k < R; ++k) tot[k] += L.part[(size_t)item * kPartRows + lane + 32 * k];
     }
-    finish_rows3<R>(L, I, fe.x, blk, r0, r1, xr, m, tot, red);
+    finish_rows3<R>(L, I, fe.x, blk, r0, r1, xr, m, tot);
 }
 
 // ------------------------------------------------------------ 3 < D <= 64 --
@@ -624,20 +645,22 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
     require(!(two && L.part), "softmin_run: split blocks need old values", OTGB_EINTERNAL);
     require(!(D > 3 && L.part), "softmin_run: split blocks are D <= 3 only", OTGB_EINTERNAL);
     if (D <= 3) {
+        const int grid = (L.n_items + kW3 - 1) / kW3;
         switch (rows_per_thread + (two ? 8 : 0)) {
-            case 1: softmin3_kernel<1, false><<<L.n_items, kNT3, 0, st>>>(L); break;
-            case 2: softmin3_kernel<2, false><<<L.n_items, kNT3, 0, st>>>(L); break;
-            case 4: softmin3_kernel<4, false><<<L.n_items, kNT3, 0, st>>>(L); break;
-            case 9: softmin3_kernel<1, true><<<L.n_items, kNT3, 0, st>>>(L); break;
-            case 10: softmin3_kernel<2, true><<<L.n_items, kNT3, 0, st>>>(L); break;
-            default: softmin3_kernel<4, true><<<L.n_items, kNT3, 0, st>>>(L); break;
+            case 1: softmin3_kernel<1, false><<<grid, 32 * kW3, 0, st>>>(L); break;
+            case 2: softmin3_kernel<2, false><<<grid, 32 * kW3, 0, st>>>(L); break;
+            case 4: softmin3_kernel<4, false><<<grid, 32 * kW3, 0, st>>>(L); break;
+            case 9: softmin3_kernel<1, true><<<grid, 32 * kW3, 0, st>>>(L); break;
+            case 10: softmin3_kernel<2, true><<<grid, 32 * kW3, 0, st>>>(L); break;
+            default: softmin3_kernel<4, true><<<grid, 32 * kW3, 0, st>>>(L); break;
         }
         OTGB_CHECK_LAUNCH();
         if (L.part && L.n_fin > 0) {
+            const int fgrid = (L.n_fin + kW3 - 1) / kW3;
             switch (rows_per_thread) {
-                case 1: softmin3_finalize_kernel<1><<<L.n_fin, kNT3, 0, st>>>(L); break;
-                case 2: softmin3_finalize_kernel<2><<<L.n_fin, kNT3, 0, st>>>(L); break;
-                default: softmin3_finalize_kernel<4><<<L.n_fin, kNT3, 0, st>>>(L); break;
+                case 1: softmin3_finalize_kernel<1><<<fgrid, 32 * kW3, 0, st>>>(L); break;
+                case 2: softmin3_finalize_kernel<2><<<fgrid, 32 * kW3, 0, st>>>(L); break;
+                default: softmin3_finalize_kernel<4><<<fgrid, 32 * kW3, 0, st>>>(L); break;
             }
             OTGB_CHECK_LAUNCH();
         }

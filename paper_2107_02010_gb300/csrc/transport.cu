@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "kmeans.cuh"
 #include "multiscale.cuh"
 #include "prims.cuh"
 #include "solver.cuh"
@@ -138,35 +139,177 @@ __global__ void __launch_bounds__(kTT) transport_kernel(const __grid_constant__ 
     if (A.mass) A.mass[r] = (float)mass;
 }
 
-// Rows whose sums fell below the safe range: one warp per (row, class), two
-// passes in the direct form.
+
+// 3 < D <= 64: 256 threads, a block of at most 128 rows (one k-means cluster
+// piece); the columns of each class form one contiguous range of the
+// label-sorted atlas and are swept in tiles of 64, register-tiled 8 rows x 4
+// columns per thread like the softmin kernel; the class sum of a row is final
+// when its range ends.
+constexpr int kTG = 256, kTBM = 128, kTBN = 64;
+struct TransportGenSmem {
+    float xs[64][kTBM];
+    float ys[64][kTBN];
+    float hs[kTBN];
+    float cen[64];
+    float mrow[kTBM];
+    float best[kTBM];
+    int bestl[kTBM];
+    float mass[kTBM];
+    float tot[kTBM];
+};
+
+__global__ void __launch_bounds__(kTG) transport_gen_kernel(const __grid_constant__ TransportArgs A, const int *blk_row0,
+                                                            const int *lab_off, int D4) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TransportGenSmem &S = *reinterpret_cast<TransportGenSmem *>(smem_raw);
+    const int t = threadIdx.x, b = blockIdx.x;
+    const int r0 = blk_row0[b], nr = min(blk_row0[b + 1] - r0, kTBM);
+    const float s = A.s;
+    for (int e = t; e < kTBM * D4; e += kTG) {
+        const int r = e / D4, k = e - r * D4;
+        S.xs[k][r] = (r < nr) ? A.rows[(size_t)(r0 + r) * D4 + k] : 0.f;
+    }
+    __syncthreads();
+    for (int k = t; k < D4; k += kTG) {
+        float acc = 0.f;
+        for (int r = 0; r < nr; ++r) acc += S.xs[k][r];
+        S.cen[k] = nr > 0 ? acc / (float)nr : 0.f;
+    }
+    __syncthreads();
+    for (int e = t; e < kTBM * D4; e += kTG) {
+        const int k = e / kTBM, r = e - k * kTBM;
+        S.xs[k][r] = (r < nr) ? S.xs[k][r] - S.cen[k] : 0.f;
+    }
+    __syncthreads();
+    if (t < kTBM) {
+        float acc = 0.f;
+        for (int k = 0; k < D4; ++k) acc = fmaf(S.xs[k][t], S.xs[k][t], acc);
+        // 2^(H_j - m + X.yt) = b_j exp((f_i + g_j - C_ij)/eps) with m = s (|xt|^2/2 - f_i)
+        S.mrow[t] = t < nr ? (float)((double)s * (0.5 * (double)acc - (double)A.f[r0 + t])) : 0.f;
+        S.best[t] = -1.f;
+        S.bestl[t] = -1;
+        S.mass[t] = 0.f;
+        S.tot[t] = 0.f;
+    }
+    __syncthreads();
+    for (int e = t; e < kTBM * D4; e += kTG) {
+        const int k = e / kTBM, r = e - k * kTBM;
+        S.xs[k][r] *= s;
+    }
+    const int tr = t >> 4, tc = t & 15;
+    float mreg[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mreg[i] = S.mrow[tr * 8 + i];
+    const int D44 = D4 >> 2;
+    for (int l = 0; l < A.L; ++l) {
+        const int lb = lab_off[l], le = lab_off[l + 1];
+        float rs[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) rs[i] = 0.f;
+        for (int p0 = lb; p0 < le; p0 += kTBN) {
+            __syncthreads();
+            for (int e = t; e < kTBN * D44; e += kTG) {
+                const int col = e % kTBN, qq = e / kTBN;
+                const int j = p0 + col;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j < le) {
+                    v = *reinterpret_cast<const float4 *>(A.cols + (size_t)j * D4 + 4 * qq);
+                    v.x -= S.cen[4 * qq]; v.y -= S.cen[4 * qq + 1]; v.z -= S.cen[4 * qq + 2]; v.w -= S.cen[4 * qq + 3];
+                }
+                S.ys[4 * qq][col] = v.x; S.ys[4 * qq + 1][col] = v.y; S.ys[4 * qq + 2][col] = v.z;
+                S.ys[4 * qq + 3][col] = v.w;
+            }
+            __syncthreads();
+            if (t < kTBN) {
+                const int j = p0 + t;
+                float acc = 0.f;
+                for (int k = 0; k < D4; ++k) acc = fmaf(S.ys[k][t], S.ys[k][t], acc);
+                S.hs[t] = j < le ? s * (fmaf(A.eps, A.col_logw[j], A.g[j]) - 0.5f * acc) : -INFINITY;
+            }
+            __syncthreads();
+            float acc[8][4];
+            const float4 h4 = *reinterpret_cast<const float4 *>(&S.hs[tc * 4]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                acc[i][0] = h4.x - mreg[i]; acc[i][1] = h4.y - mreg[i];
+                acc[i][2] = h4.z - mreg[i]; acc[i][3] = h4.w - mreg[i];
+            }
+#pragma unroll 4
+            for (int k = 0; k < D4; ++k) {
+                const float4 xa = *reinterpret_cast<const float4 *>(&S.xs[k][tr * 8]);
+                const float4 xb = *reinterpret_cast<const float4 *>(&S.xs[k][tr * 8 + 4]);
+                const float4 yv = *reinterpret_cast<const float4 *>(&S.ys[k][tc * 4]);
+                const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+                const float yy[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(xv[i], yy[jj], acc[i][jj]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                rs[i] += (ex2f_(acc[i][0]) + ex2f_(acc[i][1])) + (ex2f_(acc[i][2]) + ex2f_(acc[i][3]));
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            for (int o = 8; o > 0; o >>= 1) rs[i] += __shfl_xor_sync(0xffffffffu, rs[i], o);
+        if (tc == 0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int rr = tr * 8 + i;
+                if (rr >= nr) continue;
+                const float v = rs[i];
+                if (A.scores) A.scores[(size_t)(r0 + rr) * A.L + l] = v;
+                S.tot[rr] += v;
+                if (v > S.best[rr]) { S.best[rr] = v; S.bestl[rr] = l; }
+            }
+        }
+    }
+    __syncthreads();
+    if (t < nr) {
+        const int r = r0 + t;
+        const float tot = S.tot[t];
+        if (!(tot >= 0x1p-60f && tot <= 0x1p60f) && A.m > 0) {
+            const int k = atomicAdd(A.n_fallback, 1);
+            A.fallback[k] = make_int4(r, 0, 0, 0);
+        } else {
+            A.argmax[r] = S.bestl[t];
+            if (A.mass) A.mass[r] = tot;
+        }
+    }
+}
+
+// Rows whose sums fell outside the safe range: one warp per row, two passes
+// per class in the direct form.
 __global__ void transport_fallback_kernel(const __grid_constant__ TransportArgs A) {
     const int count = *A.n_fallback;
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += nw) {
         const int r = A.fallback[w].x;
-        const float *xi = A.rows + (size_t)r * 4;
+        const float *xi = A.rows + (size_t)r * A.stride;
         double mass = 0.0, best = -1.0;
         int bestl = -1;
         for (int l = 0; l < A.L; ++l) {
             float m = -INFINITY;
             for (int j = lane; j < A.m; j += 32) {
                 if (A.col_lab[j] != l) continue;
-                const float *yj = A.cols + (size_t)j * 4;
+                const float *yj = A.cols + (size_t)j * A.stride;
                 float d2 = 0.f;
                 for (int k = 0; k < A.D; ++k) { const float u = xi[k] - yj[k]; d2 = fmaf(u, u, d2); }
-                m = fmaxf(m, A.s * (fmaf(A.eps, yj[3], A.g[j]) - 0.5f * d2));
+                const float lw = A.col_logw ? A.col_logw[j] : yj[3];
+                m = fmaxf(m, A.s * (fmaf(A.eps, lw, A.g[j]) - 0.5f * d2));
             }
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
             double acc = 0.0;
             if (m > -INFINITY)
                 for (int j = lane; j < A.m; j += 32) {
                     if (A.col_lab[j] != l) continue;
-                    const float *yj = A.cols + (size_t)j * 4;
+                    const float *yj = A.cols + (size_t)j * A.stride;
                     float d2 = 0.f;
                     for (int k = 0; k < A.D; ++k) { const float u = xi[k] - yj[k]; d2 = fmaf(u, u, d2); }
-                    acc += (double)exp2f(A.s * (fmaf(A.eps, yj[3], A.g[j]) - 0.5f * d2) - m);
+                    const float lw = A.col_logw ? A.col_logw[j] : yj[3];
+                    acc += (double)exp2f(A.s * (fmaf(A.eps, lw, A.g[j]) - 0.5f * d2) - m);
                 }
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             const double v = (m > -INFINITY) ? exp2((double)A.s * A.f[r] + m + log2(acc)) : 0.0;
@@ -179,6 +322,17 @@ __global__ void transport_fallback_kernel(const __grid_constant__ TransportArgs 
             if (A.mass) A.mass[r] = (float)mass;
         }
     }
+}
+
+__global__ void label_hist_kernel(const uint32_t *sorted_keys, int m, int L, int *off) {
+    // off[l] = first sorted position with label >= l (labels sorted ascending)
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int cur = (int)sorted_keys[j];
+    const int prev = j > 0 ? (int)sorted_keys[j - 1] : -1;
+    for (int l = prev + 1; l <= cur && l <= L; ++l) off[l] = j;
+    if (j == m - 1)
+        for (int l = cur + 1; l <= L; ++l) off[l] = m;
 }
 
 __global__ void label_sort_keys_kernel(const int *labels, int m, int L, uint32_t *keys) {
@@ -213,8 +367,8 @@ extern "C" int transport_apply(otgb_ctx *ctx, const otgb_plan *plan, const float
         require(plan != nullptr, "transport_apply: null plan");
         require(f && g && labels && argmax, "transport_apply: null pointer argument");
         require(L >= 1 && L <= 1024, "transport_apply: L must be in [1, 1024]");
-        require(plan->D <= 3, "transport_apply: D > 3 is served by the tensor-core build only");
         const int N = plan->N, M = plan->M, D = plan->D;
+        const int stride = D <= 3 ? 4 : ((D + 3) & ~3);
         cudaStream_t st = ctx_stream(ctx);
         Workspace &ws = ctx_ws(ctx);
         // centre of the columns
@@ -237,25 +391,13 @@ extern "C" int transport_apply(otgb_ctx *ctx, const otgb_plan *plan, const float
         while ((1 << bits) < L + 1) ++bits;
         void *scr = ws.get("sort:scratch", radix_sort_scratch_bytes(std::max(N, M)));
         radix_sort_pairs(keys, cperm, M, bits, scr, st);
-        float *C = ws.get<float>("ta:C", (size_t)M * 4);
+        float *C = ws.get<float>("ta:C", (size_t)M * stride);
+        float *Clw = D > 3 ? ws.get<float>("ta:Clw", M) : nullptr;
         float *gs = ws.get<float>("ta:g", M);
-        pack_points(plan->y, plan->b, cperm, M, D, d_cen, C, nullptr, nullptr, st);
+        pack_points(plan->y, plan->b, cperm, M, D, d_cen, C, Clw, nullptr, st);
         permute(g, cperm, M, gs, st);
-        // rows in Morton order of a fine grid (compact CTAs)
-        float *Rw = ws.get<float>("ta:R", (size_t)N * 4);
+        float *Rw = ws.get<float>("ta:R", (size_t)N * stride);
         float *fs = ws.get<float>("ta:f", N);
-        float *rlo = ws.get<float>("ta:rlo", 128);
-        bbox(plan->x, N, D, D, rlo, rlo + 64, bpart, st);
-        std::vector<float> hb(128);
-        OTGB_CUDA_TRY(cudaMemcpyAsync(hb.data(), rlo, 128 * sizeof(float), cudaMemcpyDeviceToHost, st));
-        OTGB_CUDA_TRY(cudaStreamSynchronize(st));
-        float ext = 0.f;
-        for (int d = 0; d < D; ++d) ext = std::max(ext, hb[64 + d] - hb[d]);
-        int per_axis = std::max(1, std::min(512, (int)std::ceil(std::cbrt((double)N / 4.0))));
-        const float cell = ext > 0.f ? ext / (float)per_axis * 1.0001f : 1.0f;
-        GridClusters gc = grid_cluster(ctx, "ta:rows", plan->x, N, D, cell, rlo);
-        pack_points(plan->x, nullptr, gc.perm, N, D, d_cen, Rw, nullptr, nullptr, st);
-        permute(f, gc.perm, N, fs, st);
         float *sc = scores ? ws.get<float>("ta:sc", (size_t)N * L) : nullptr;
         int *am = ws.get<int>("ta:am", N);
         float *ms = ws.get<float>("ta:ms", N);
@@ -264,17 +406,61 @@ extern "C" int transport_apply(otgb_ctx *ctx, const otgb_plan *plan, const float
         OTGB_CUDA_TRY(cudaMemsetAsync(nfb, 0, sizeof(int), st));
         TransportArgs A;
         std::memset(&A, 0, sizeof(A));
-        A.rows = Rw; A.f = fs; A.cols = C; A.g = gs; A.col_lab = reinterpret_cast<const int *>(keys);
-        A.n = N; A.m = M; A.D = D; A.stride = 4; A.L = L;
+        A.cols = C; A.col_logw = Clw; A.g = gs; A.col_lab = reinterpret_cast<const int *>(keys);
+        A.n = N; A.m = M; A.D = D; A.stride = stride; A.L = L;
         A.eps = (float)plan->eps;
         A.s = (float)(1.4426950408889634 / plan->eps);
         A.eps_ln2 = plan->eps * 0.69314718055994530942;
         A.scores = sc; A.argmax = am; A.mass = ms; A.fallback = fb; A.n_fallback = nfb;
-        transport_kernel<<<(N + kTT - 1) / kTT, kTT, 0, st>>>(A);
-        OTGB_CHECK_LAUNCH();
+        const int *row_perm = nullptr;
+        if (D <= 3) {
+            // rows in Morton order of a fine grid (compact CTAs)
+            float *rlo = ws.get<float>("ta:rlo", 128);
+            bbox(plan->x, N, D, D, rlo, rlo + 64, bpart, st);
+            std::vector<float> hb(128);
+            OTGB_CUDA_TRY(cudaMemcpyAsync(hb.data(), rlo, 128 * sizeof(float), cudaMemcpyDeviceToHost, st));
+            OTGB_CUDA_TRY(cudaStreamSynchronize(st));
+            float ext = 0.f;
+            for (int d = 0; d < D; ++d) ext = std::max(ext, hb[64 + d] - hb[d]);
+            int per_axis = std::max(1, std::min(512, (int)std::ceil(std::cbrt((double)N / 4.0))));
+            const float cell = ext > 0.f ? ext / (float)per_axis * 1.0001f : 1.0f;
+            GridClusters gc = grid_cluster(ctx, "ta:rows", plan->x, N, D, cell, rlo);
+            row_perm = gc.perm;
+            pack_points(plan->x, nullptr, gc.perm, N, D, d_cen, Rw, nullptr, nullptr, st);
+            permute(f, gc.perm, N, fs, st);
+            A.rows = Rw; A.f = fs;
+            transport_kernel<<<(N + kTT - 1) / kTT, kTT, 0, st>>>(A);
+            OTGB_CHECK_LAUNCH();
+        } else {
+            // rows ordered by a short K-means; blocks of <= 128 rows inside clusters
+            const int K = std::max(1, std::min(N / 64, 4096));
+            KmeansResult kr = kmeans(ctx, "ta:km", plan->x, nullptr, N, D, K, 4, 12345, nullptr);
+            std::vector<int> off(K + 1);
+            OTGB_CUDA_TRY(cudaMemcpyAsync(off.data(), kr.offsets, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, st));
+            OTGB_CUDA_TRY(cudaStreamSynchronize(st));
+            std::vector<int> hb = make_row_blocks(N, 128, &off);
+            int *d_blk = ws.get<int>("ta:blk", hb.size());
+            OTGB_CUDA_TRY(cudaMemcpyAsync(d_blk, hb.data(), sizeof(int) * hb.size(), cudaMemcpyHostToDevice, st));
+            int *lab_off = ws.get<int>("ta:laboff", L + 1);
+            label_hist_kernel<<<(M + 255) / 256, 256, 0, st>>>(keys, M, L, lab_off);
+            OTGB_CHECK_LAUNCH();
+            row_perm = kr.perm;
+            pack_points(plan->x, nullptr, kr.perm, N, D, d_cen, Rw, nullptr, nullptr, st);
+            permute(f, kr.perm, N, fs, st);
+            A.rows = Rw; A.f = fs;
+            static bool attr = false;
+            if (!attr) {
+                OTGB_CUDA_TRY(cudaFuncSetAttribute(transport_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sizeof(TransportGenSmem)));
+                attr = true;
+            }
+            transport_gen_kernel<<<(int)hb.size() - 1, kTG, sizeof(TransportGenSmem), st>>>(A, d_blk, lab_off, stride);
+            OTGB_CHECK_LAUNCH();
+            OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // hb, off released
+        }
         transport_fallback_kernel<<<64, 256, 0, st>>>(A);
         OTGB_CHECK_LAUNCH();
-        unpermute_rows_kernel<<<(N + 255) / 256, 256, 0, st>>>(sc, am, ms, gc.perm, N, L, scores, argmax, row_mass);
+        unpermute_rows_kernel<<<(N + 255) / 256, 256, 0, st>>>(sc, am, ms, row_perm, N, L, scores, argmax, row_mass);
         OTGB_CHECK_LAUNCH();
         OTGB_CUDA_TRY(cudaStreamSynchronize(st));
         return OTGB_OK;

@@ -46,6 +46,7 @@ class Params(C.Structure):
         ("sigma_start", C.c_double),
         ("translation", C.c_int),
         ("anderson", C.c_int),
+        ("rows_per_thread", C.c_int),
     ]
 
 

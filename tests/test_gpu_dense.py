@@ -324,3 +324,26 @@ def test_transport_apply_matches_oracle(ctx):
     top2 = np.sort(rsc, axis=1)[:, -2:]
     clear = top2[:, 1] - top2[:, 0] >= 1e-4 * top2[:, 1]
     assert np.all(am.cpu().numpy()[clear] == ram[clear])
+
+
+def test_transport_apply_fibers_identical_argmax(ctx):
+    # 60-D label transfer by the smooth plan (Eq. (7)): scores against the
+    # oracle and identical argmax labels on rows with a clear top class
+    from paper_2107_02010_gb300 import otgb
+
+    ctrl = synth.bundle_centrelines()
+    x, a, _ = synth.fiber_bundles(600, seed=4, ctrl=ctrl, perturb=3.0)
+    y, b, lab = synth.fiber_bundles(500, seed=5, ctrl=ctrl)
+    blur, reach, L = 2.0, 20.0, 20
+    out = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b), otgb.default_params(blur=blur, reach=reach, tol=1e-7),
+                                   want_plan=True)
+    f64 = out["f"].cpu().numpy().astype(np.float64)
+    g64 = out["g"].cpu().numpy().astype(np.float64)
+    sc, am, rm = otgb.transport_apply(ctx, out["plan"], out["f"], out["g"], T(lab), L)
+    rsc, ram, rrm = oracle.transport_apply(x, y, b, blur ** 2, f64, g64, lab, L)
+    np.testing.assert_allclose(sc.cpu().numpy(), rsc, rtol=1e-4, atol=1e-5 * rsc.max())
+    np.testing.assert_allclose(rm.cpu().numpy(), rrm, rtol=1e-4)
+    top2 = np.sort(rsc, axis=1)[:, -2:]
+    clear = top2[:, 1] - top2[:, 0] >= 1e-4 * top2[:, 1]
+    print("rows with a clear top class:", int(clear.sum()), "of", len(clear))
+    assert np.all(am.cpu().numpy()[clear] == ram[clear])
