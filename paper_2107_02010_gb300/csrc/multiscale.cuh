@@ -53,6 +53,7 @@ struct Solver {
     double S = 0.0, last_delta = 0.0, last_rel = 0.0, last_potmax = 0.0;
     bool timing = false;
     bool translation = false;
+    bool use_tc = false;
     std::vector<cudaEvent_t> ev_pool;
     int ev_used = 0;
     double softmin_ms = 0.0;

@@ -131,6 +131,8 @@ struct SoftminLaunch {
     int n_items;
     float *part;             // null: every block is a single item, finished inline
     int exact_max;           // 1: take each row's shift from an exact maximum pass even when old values exist
+    int use_tc;              // 1: D >= 16 cross term on the tensor cores (BF16 hi/lo split, FP32 accumulate)
+    unsigned int *tc_err;    // set when a bounded tensor-core wait gave up (may be null)
     const int4 *fin;         // finalize list (split mode)
     int n_fin;
     float eps;               // temperature
@@ -148,6 +150,10 @@ struct SoftminLaunch {
 // any flagged rows (no host synchronisation; capturable in a CUDA graph).
 // D selects the specialisation.  Errors throw otgb::Error.
 void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_t st);
+
+// Tensor-core softmin (softmin_tc.cu), D >= 16, old values required, blocks <= 128 rows.
+void softmin_tc_launch(const SoftminLaunch &L, int D, cudaStream_t st);
+size_t softmin_tc_smem_bytes();
 
 // Build uniform row blocks of `block_rows` rows for an instance of n rows:
 // writes blk_row0 (n_blocks+1) on the device.  Returns n_blocks.

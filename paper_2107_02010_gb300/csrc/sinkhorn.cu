@@ -264,6 +264,9 @@ void Solver::alloc_common() {
     d_fb_total = ws->get<unsigned long long>(nm("fbtot"), 1);
     launch.fallback_total = d_fb_total;
     d_pairs = ws->get<unsigned long long>(nm("pairs"), 1);
+    launch.tc_err = ws->get<unsigned>(nm("tcerr"), 1);
+    OTGB_CUDA_TRY(cudaMemsetAsync(launch.tc_err, 0, sizeof(unsigned), st));
+    launch.use_tc = use_tc ? 1 : 0;
     OTGB_CUDA_TRY(cudaMemsetAsync(d_fb_total, 0, sizeof(unsigned long long), st));
     OTGB_CUDA_TRY(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
     if (timing && ev_pool.empty()) {
@@ -424,6 +427,7 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         s.rho = (!(P.reach > 0.0) || std::isinf(P.reach)) ? INFINITY : P.reach * P.reach;
         s.timing = stats != nullptr;
         s.translation = P.translation != 0;
+        s.use_tc = P.precision == OTGB_TC_BF16X3 && D >= 16;
         cudaStream_t st = s.st;
         OTGB_CUDA_TRY(cudaEventRecord(ctx_event(ctx, 0), st));
 
@@ -459,9 +463,12 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
             s.Y.perm = spatial_sort(ctx, "sy", y, M, D, chk.loy, chk.hiy, d_box + 128);
         } else {
             // compact row blocks in high dimension: order the points by a short
-            // K-means (about 16 points per cluster) and keep blocks inside clusters
+            // K-means and keep blocks inside clusters (about 16 points per cluster
+            // for the float32 kernel; about 128, one full tensor-core tile, for the
+            // tensor-core form)
+            const int per = s.use_tc ? 128 : 16;
             auto order = [&](const char *tag, const float *pts, const float *w, int n, std::vector<int> &off) {
-                const int K = std::max(1, std::min(n / 16, 8192));
+                const int K = std::max(1, std::min(n / per, 8192));
                 KmeansResult r = kmeans(ctx, tag, pts, w, n, D, K, 4, P.seed, nullptr);
                 off.resize(K + 1);
                 OTGB_CUDA_TRY(cudaMemcpyAsync(off.data(), r.offsets, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, st));
@@ -527,11 +534,13 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         OTGB_CUDA_TRY(cudaMemcpyAsync(mb + kMbBad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
         OTGB_CUDA_TRY(cudaMemcpyAsync(mb + kMbMass, s.d_pairs, 8, cudaMemcpyDeviceToHost, st));
         OTGB_CUDA_TRY(cudaMemcpyAsync(mb + kMbMass + 8, s.d_fb_total, 8, cudaMemcpyDeviceToHost, st));
+        OTGB_CUDA_TRY(cudaMemcpyAsync(mb + kMbMass + 16, s.launch.tc_err, 4, cudaMemcpyDeviceToHost, st));
         OTGB_CUDA_TRY(cudaEventRecord(ctx_event(ctx, 1), st));
         OTGB_CUDA_TRY(cudaStreamSynchronize(st));
         s.harvest_timing();
         *cost_host = s.S;
         if (*reinterpret_cast<int *>(mb + kMbBad) || !std::isfinite(s.S)) rc = OTGB_ENONFINITE;
+        if (*reinterpret_cast<unsigned *>(mb + kMbMass + 16)) rc = OTGB_ETIMEOUT;
 
         if (plan_out && (rc == OTGB_OK || rc == OTGB_ENOCONV)) {
             otgb_plan *pl = new otgb_plan();
@@ -566,8 +575,9 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
             stats->fallback_rows = (long long)fbt;
         }
         if (rc != OTGB_OK) {
-            const char *m = rc == OTGB_ENOCONV ? "sinkhorn_divergence: max_iters reached before the stopping rule held"
-                                               : "sinkhorn_divergence: a potential or the divergence is not finite";
+            const char *m = rc == OTGB_ENOCONV   ? "sinkhorn_divergence: max_iters reached before the stopping rule held"
+                            : rc == OTGB_ETIMEOUT ? "sinkhorn_divergence: a bounded tensor-core wait gave up"
+                                                  : "sinkhorn_divergence: a potential or the divergence is not finite";
             return fail(ctx, Error{rc, m});
         }
         return OTGB_OK;

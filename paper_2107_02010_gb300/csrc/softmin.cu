@@ -674,9 +674,15 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
                                                (int)sizeof(GenSmem)));
             attr = true;
         }
-        if (two) softmin_gen_kernel<true><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
-        else softmin_gen_kernel<false><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
-        OTGB_CHECK_LAUNCH();
+        if (two) {
+            softmin_gen_kernel<true><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
+            OTGB_CHECK_LAUNCH();
+        } else if (L.use_tc && D >= 16) {
+            softmin_tc_launch(L, D, st);
+        } else {
+            softmin_gen_kernel<false><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
+            OTGB_CHECK_LAUNCH();
+        }
     }
     const int stride = D <= 3 ? 4 : ((D + 3) & ~3);
     softmin_fallback_kernel<<<64, 256, 0, st>>>(L, D, stride);

@@ -1,0 +1,75 @@
+"""The tensor-core form (tcgen05 BF16 hi/lo cross term, FP32 accumulation and
+log-sum-exp) against the FP64 oracle, to the reduced-precision bar of 1e-3
+relative on S and the duals, with identical transferred labels on rows whose
+top class is clear."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2107_02010_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL_TC = 1e-3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2107_02010_gb300 import otgb
+
+    c = otgb.Context()
+    yield c
+    c.close()
+
+
+def T(v):
+    return torch.from_numpy(np.ascontiguousarray(v)).cuda()
+
+
+def rel(got, want, eps):
+    got = got.detach().cpu().numpy().astype(np.float64) if torch.is_tensor(got) else np.asarray(got, np.float64)
+    return float(np.max(np.abs(got - want)) / (np.max(np.abs(want)) + eps))
+
+
+def test_tensorcore_fixed_steps_match_oracle(ctx):
+    from paper_2107_02010_gb300 import otgb
+
+    ctrl = synth.bundle_centrelines()
+    x, a, _ = synth.fiber_bundles(700, seed=4, ctrl=ctrl, perturb=3.0)
+    y, b, _ = synth.fiber_bundles(650, seed=5, ctrl=ctrl)
+    blur, reach, q, extra = 2.0, 20.0, 0.5, 8
+    d = oracle.diameter(x, y)
+    n_sched = len(oracle.schedule(d, blur, q))
+    p = otgb.default_params(blur=blur, reach=reach, scaling=q, diameter=d, fixed_iters=extra, translation=0,
+                            anderson=0, precision=1)
+    out = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b), p, want_self=True)
+    ref = oracle.sinkhorn(x, a, y, b, blur=blur, reach=reach, scaling=q, diameter=d, tol=0.0,
+                          max_iters=n_sched + extra)
+    eps = blur ** 2
+    errs = {k: rel(out[k], ref[key], eps) for k, key in (("f", "f"), ("g", "g"), ("a_self", "a"), ("b_self", "b"))}
+    print("tensor-core errors", errs, "S", out["S"], ref["S"])
+    for k, v in errs.items():
+        assert v < TOL_TC, (k, errs)
+    assert abs(out["S"] - ref["S"]) <= TOL_TC * abs(ref["S"])
+
+
+def test_tensorcore_converged_labels(ctx):
+    from paper_2107_02010_gb300 import otgb
+
+    ctrl = synth.bundle_centrelines()
+    x, a, _ = synth.fiber_bundles(900, seed=6, ctrl=ctrl, perturb=3.0)
+    y, b, lab = synth.fiber_bundles(800, seed=7, ctrl=ctrl)
+    blur, reach, L = 2.0, 20.0, 20
+    fp32 = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b), otgb.default_params(blur=blur, reach=reach,
+                                                                                     tol=1e-7))
+    tc = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b),
+                                  otgb.default_params(blur=blur, reach=reach, tol=1e-7, precision=1), want_plan=True)
+    print("fp32", fp32["stats"], "\ntc", tc["stats"])
+    assert abs(tc["S"] - fp32["S"]) <= TOL_TC * abs(fp32["S"])
+    f64 = tc["f"].cpu().numpy().astype(np.float64)
+    g64 = tc["g"].cpu().numpy().astype(np.float64)
+    sc, am, rm = otgb.transport_apply(ctx, tc["plan"], tc["f"], tc["g"], T(lab), L)
+    rsc, ram, rrm = oracle.transport_apply(x, y, b, blur ** 2, f64, g64, lab, L)
+    top2 = np.sort(rsc, axis=1)[:, -2:]
+    clear = top2[:, 1] - top2[:, 0] >= 1e-4 * top2[:, 1]
+    assert np.all(am.cpu().numpy()[clear] == ram[clear])
