@@ -9,6 +9,11 @@ time (all four symmetric instances, whole solve: clustering, coarse phase,
 extrapolation, truncation, fine steps, final FP64 sums).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Other workloads (not the default line; each prints its own JSON line):
+    --workload fibers [--n N] [--precision fp32|tc]   60-D fiber bundles, k-means multiscale,
+        blur 2 mm, reach 20 mm (FP32 or the BF16 hi/lo tensor-core cross term)
+    --workload mlp [--n N]    warm-start network: inference and training throughput
 """
 from __future__ import annotations
 
@@ -39,6 +44,21 @@ def workload(args):
 
     x, a, y, b = synth.density_maps(grid=args.grid, n_keep=args.n_keep)
     return x, a, y, b
+
+
+def fiber_workload(args):
+    from paper_2107_02010_gb300 import synth
+
+    ctrl = synth.bundle_centrelines()
+    x, a, _ = synth.fiber_bundles(args.n, seed=4, ctrl=ctrl, perturb=3.0)
+    y, b, _ = synth.fiber_bundles(args.n, seed=5, ctrl=ctrl)
+    return x, a, y, b
+
+
+def fiber_params(args, otgb):
+    return otgb.default_params(blur=2.0, reach=20.0, scaling=0.5, multiscale=1, cluster=1,
+                               k_clusters=max(20, args.n // 1000), kmeans_iters=10, tol=args.tol,
+                               max_iters=args.max_iters, precision=1 if args.precision == "tc" else 0)
 
 
 def params_for(args, otgb):
@@ -118,6 +138,106 @@ def peak_pairs_per_s(D, clock_mhz, n_sm):
     return per_clk * n_sm * clock_mhz * 1e6
 
 
+def run_mlp(args):
+    """Warm-start network throughput: inference over n rows and one training
+    epoch over n rows (batches of 16384), FLOPs counted as 2 per multiply-add of
+    the four layers (input padded to 64); training = 3 x forward."""
+    import torch
+    from paper_2107_02010_gb300 import otgb
+
+    ctx = otgb.Context()
+    D, H = 60, 256
+    net = otgb.Mlp(ctx, D, H, seed=1)
+    r = np.random.default_rng(0)
+    n = args.n
+    x = torch.from_numpy(r.normal(0, 1, (n, D)).astype(np.float32)).cuda()
+    f = torch.from_numpy(r.normal(0, 1, n).astype(np.float32)).cuda()
+    fwd = 2.0 * n * (64 * H + 2 * H * H + H)
+    for _ in range(args.warmup):
+        net.infer(x)
+        net.train_epoch(x, f, 16384, 1e-4, seed=0)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    l0 = otgb.kernel_launches()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(st)
+    for _ in range(args.steps):
+        net.infer(x)
+    ev[1].record(st)
+    ev[2].record(st)
+    for k in range(args.steps):
+        net.train_epoch(x, f, 16384, 1e-4, seed=k + 1)
+    ev[3].record(st)
+    torch.cuda.synchronize()
+    inf_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    tr_ms = ev[2].elapsed_time(ev[3]) / args.steps
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    line = {"metric": "warm-start network TFLOP/s", "workload": "mlp", "unit": "TFLOP/s",
+            "value": fwd / inf_ms / 1e9, "steps": args.steps, "warmup": args.warmup, "dtype": "bf16",
+            "data": "synthetic", "higher_is_better": True,
+            "config": {"workload": "MLP %d->%d->%d->%d->1 SiLU, %d rows" % (D, H, H, H, n)},
+            "inference_ms": inf_ms, "inference_tflops": fwd / inf_ms / 1e9,
+            "train_epoch_ms": tr_ms, "train_tflops": 3 * fwd / tr_ms / 1e9,
+            "roofline": {"bound": "tensor", "peak": peak, "unit": "TFLOP/s",
+                         "frac_inference": fwd / inf_ms / 1e9 / peak, "frac_train": 3 * fwd / tr_ms / 1e9 / peak,
+                         "peak_basis": "bf16 burst, of measured"},
+            "gpu_launches": int(otgb.kernel_launches() - l0)}
+    print(json.dumps(line))
+    return 0
+
+
+def run_fibers(args):
+    """60-D fiber bundles (N = M = n), k-means multiscale, FP32 or tensor-core
+    form; one step = one solve to the stopping rule."""
+    import torch
+    from paper_2107_02010_gb300 import otgb
+
+    x, a, y, b = fiber_workload(args)
+    X, A, Y, B = (torch.from_numpy(v).cuda() for v in (x, a, y, b))
+    ctx = otgb.Context()
+    p = fiber_params(args, otgb)
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        out = otgb.sinkhorn_divergence(ctx, X, A, Y, B, p, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    sampler, sf = start_clock_sampler()
+    st = torch.cuda.current_stream()
+    l0 = otgb.kernel_launches()
+    ms, pairs, smin = [], 0.0, 0.0
+    for _ in range(args.steps):
+        flush_l2(l2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        out = otgb.sinkhorn_divergence(ctx, X, A, Y, B, p, raise_on_noconv=False)
+        e1.record(st)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        pairs += out["stats"]["pairs_evaluated"]
+        smin += out["stats"]["softmin_ms"]
+    clocks = stop_clock_sampler(sampler, sf)
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    clk = peaks.get("sm_max_mhz", 2070.0)
+    D = x.shape[1]
+    peak = peak_pairs_per_s(D, clk, n_sm)
+    achieved = pairs / (smin / 1e3) if smin > 0 else None
+    line = {"metric": "softmin pairs/s", "workload": "fibers", "value": pairs / (sum(ms) / 1e3), "unit": "pairs/s",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+            "higher_is_better": True, "dtype": "f32" if args.precision == "fp32" else "bf16x3+f32",
+            "data": "synthetic",
+            "config": {"workload": "fiber bundles 60-D, N=M=%d, k-means %d clusters, blur 2, reach 20, q 0.5, %s" %
+                                   (args.n, max(20, args.n // 1000), args.precision)},
+            "time_to_solve_ms": statistics.mean(ms), "iters_per_solve": out["stats"]["iters_total"],
+            "S": out["S"], "last_stats": out["stats"],
+            "roofline": {"bound": "alu", "achieved": achieved / 1e9 if achieved else None, "peak": peak / 1e9,
+                         "unit": "Gpairs/s", "frac": achieved / peak if achieved else None,
+                         "peak_basis": "FP32 form: %d SMs x min(32, 128/(D+2)) pairs/clk x %.0f MHz" % (n_sm, clk)},
+            "gpu_launches": int(otgb.kernel_launches() - l0), "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -157,9 +277,19 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows-per-thread", type=int, default=0)
+    ap.add_argument("--workload", default="density", choices=["density", "fibers", "mlp"])
+    ap.add_argument("--n", type=int, default=0, help="fibers: points per side (200000); mlp: rows (1048576)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tc"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "fibers":
+        args.n = args.n or 200_000
+        args.max_iters = min(args.max_iters, 5000)
+        return run_fibers(args)
+    if args.workload == "mlp":
+        args.n = args.n or (1 << 20)
+        return run_mlp(args)
 
     import torch
 

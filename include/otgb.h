@@ -82,6 +82,11 @@ typedef struct {
                               Default 5. */
     int rows_per_thread;   /* D <= 3 kernel tuning: rows per thread (1, 2 or 4; a block holds 128 x this many
                               rows); 0 = automatic (4 dense, 2 multiscale). */
+    int init_g_from_f;     /* 1 with f_init and no g_init: g starts as one plain softmin of f at the first
+                              scale, g_j = -lam eps log sum_i alpha_i exp((f_i - C(x_i, y_j)) / eps), instead
+                              of 0.  Default 0. */
+    int warm_max_iters;    /* sinkhorn_divergence_warm: step budget of the warm attempt before it falls
+                              back to the plain solve; <= 0: max_iters.  Default 0. */
 } otgb_params;
 
 /* Statistics of one solve (host struct, filled when non-null). */
@@ -101,6 +106,10 @@ typedef struct {
     double last_delta;       /* last max |new - old| / eps over the four vectors */
     double last_rel_change;  /* last estimated remaining relative change of S */
     long long fallback_rows; /* rows recomputed by the safe two-pass kernel */
+    int warm_start;          /* sinkhorn_divergence_warm: 1 = the warm attempt converged, 2 = it fell back to
+                                the plain solve (the other fields then describe the plain solve); 0 otherwise */
+    int warm_iters;          /* steps spent in the warm attempt */
+    double warm_ms;          /* device time of the warm attempt and the network's inference */
 } otgb_stats;
 
 /* Fill *p with defaults: p = 2, blur = 0.05, reach = 0 (balanced), scaling = 0.5,
@@ -237,6 +246,81 @@ int otgb_softmin(otgb_ctx *ctx, const float *q, int n_out, const float *p, const
 int otgb_softmin_noalloc(const float *q, int n_out, const float *p, const float *w, const float *pot, int n_in,
                          int D, double eps, double lam, const float *old, double omega, float *out,
                          void *cuda_stream);
+
+/*
+ * Warm-start network (an addition; the paper has no learned component).  A
+ * multilayer perceptron f(x) = out_mean + out_scale * MLP((x - in_mean) / in_scale),
+ * D -> H -> H -> H -> 1 with SiLU activations, learns the subject-side dual f of
+ * the transport problem against one fixed atlas from potentials the solver
+ * produced; sinkhorn_divergence_warm uses it only as the initial f at the final
+ * temperature, and the Sinkhorn iterations decide the result.
+ *
+ * Arithmetic: every layer is a tensor-core GEMM with BF16 operands (weights,
+ * activations, gradients of the pre-activations) and FP32 accumulation; biases,
+ * the head, the loss and the Adam state are FP32; the master weights are FP32.
+ * Flat parameter vector (n_params floats, FP32): W1 (H x D, row-major, rows =
+ * outputs), b1 (H), W2 (H x H), b2, W3 (H x H), b3, W4 (1 x H), b4 (1).
+ * Loss: L = (1/2n) sum_i ((MLP_i - (f_i - out_mean)) / out_scale)^2, i.e. half the
+ * mean squared error in normalised units.  Adam: beta1 = 0.9, beta2 = 0.999,
+ * eps = 1e-8, with bias correction (Kingma & Ba 2015).
+ * The network belongs to one context and runs on its stream; it owns its
+ * device memory until otgb_mlp_destroy.
+ */
+typedef struct otgb_mlp otgb_mlp;
+
+/* D in [1, 64], hidden in {128, 256}; weights uniform in +-sqrt(6/fan_in)
+   (head +-sqrt(3/H)) from `seed`, biases 0, identity normalisation. */
+int otgb_mlp_create(otgb_ctx *ctx, int D, int hidden, unsigned long long seed, otgb_mlp **out);
+int otgb_mlp_destroy(otgb_mlp *mlp);
+/* Number of FP32 parameters (or -1 for a null handle). */
+int otgb_mlp_n_params(const otgb_mlp *mlp);
+/* Normalisation from data: per-feature mean and standard deviation of x (n x D,
+   device) and of f (n, device; NULL keeps the output normalisation).  A feature
+   with zero spread gets scale 1. */
+int otgb_mlp_fit_normalization(otgb_mlp *mlp, const float *x, const float *f, int n);
+/* host arrays of D floats; scales > 0 */
+int otgb_mlp_set_normalization(otgb_mlp *mlp, const float *in_mean, const float *in_scale, double out_mean,
+                               double out_scale);
+int otgb_mlp_get_normalization(const otgb_mlp *mlp, float *in_mean, float *in_scale, double *out_mean,
+                               double *out_scale);
+/* Host copy of the FP32 master parameters (n must equal n_params).  set also
+   clears the Adam state. */
+int otgb_mlp_set_params(otgb_mlp *mlp, const float *theta_host, int n);
+int otgb_mlp_get_params(const otgb_mlp *mlp, float *theta_host, int n);
+/* Loss (host, optional) and its gradient (device, n_params floats) over the n
+   rows (x: n x D, f: n, device), 1 <= n <= 65536.  No update. */
+int otgb_mlp_grad(otgb_mlp *mlp, const float *x, const float *f, int n, double *loss, float *grad);
+/* One Adam update with a caller-supplied gradient (device, n_params floats). */
+int otgb_mlp_adam_step(otgb_mlp *mlp, const float *grad, float lr);
+/* otgb_mlp_grad on the n rows followed by one Adam update; loss optional (host). */
+int otgb_mlp_train_step(otgb_mlp *mlp, const float *x, const float *f, int n, float lr, double *loss);
+/* One pass over n rows in a seeded random order, batches of `batch` rows
+   (128 <= batch <= 65536; the last batch may be smaller), one Adam update per
+   batch.  mean_loss (host, optional): the row-weighted mean of the batch losses. */
+int otgb_mlp_train_epoch(otgb_mlp *mlp, const float *x, const float *f, int n, int batch, float lr,
+                         unsigned long long seed, double *mean_loss);
+/* out (device, n) = f(x) in data units; x: n x D device. */
+int otgb_mlp_infer(otgb_mlp *mlp, const float *x, int n, float *out);
+/* Binary file: header (magic "OTGBMLP1", D, H, n_params, Adam step, normalisation)
+   then FP32 parameters and Adam moments.  load requires matching D and H. */
+int otgb_mlp_save(const otgb_mlp *mlp, const char *path);
+int otgb_mlp_load(otgb_mlp *mlp, const char *path);
+
+/*
+ * Warm-started solve: f0 = network(x); the solve then starts at sigma = blur with
+ * f = f0, g = one plain softmin of f0 (init_g_from_f), b = b_atlas when given (the
+ * atlas' own symmetric dual from an earlier solve against the same y and b; it
+ * depends on y and b only) and a = 0, and iterates the averaged loop at blur
+ * with the stopping rule of sinkhorn_divergence.  When that attempt ends with
+ * ENOCONV (params->warm_max_iters steps), ENONFINITE or ETIMEOUT, the plain
+ * solve with *params runs instead.  Arguments and outputs as in
+ * sinkhorn_divergence; mlp must belong to ctx and have D inputs.  stats->warm_start
+ * tells which path produced the outputs.
+ */
+int sinkhorn_divergence_warm(otgb_ctx *ctx, otgb_mlp *mlp, const float *x, const float *a, int N, const float *y,
+                             const float *b, int M, int D, const otgb_params *params, const float *b_atlas,
+                             double *cost_host, float *f, float *g, float *a_self, float *b_self,
+                             otgb_plan **plan_out, otgb_stats *stats);
 
 /* Number of CUDA kernels this library has launched in this process (all
    contexts), for accounting by benchmarks. */

@@ -98,21 +98,31 @@ __global__ void __launch_bounds__(kAT) kmeans_assign_kernel(const float *x, int 
     }
 }
 
-__global__ void kmeans_accum_kernel(const float *x, const float *w, int n, int D, const int *labels, float *sum,
-                                    float *mass, int D4) {
-    const int i = blockIdx.x, t = threadIdx.x;
-    if (i >= n) return;
-    const int k = labels[i];
-    const float wi = w ? w[i] : 1.f;
-    for (int d = t; d < D; d += blockDim.x) atomicAdd(&sum[(size_t)k * D4 + d], wi * x[(size_t)i * D + d]);
-    if (t == 0) atomicAdd(&mass[k], wi);
-}
-
-__global__ void kmeans_update_kernel(float *cent, const float *sum, const float *mass, int K, int D, int D4) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= K * D) return;
-    const int k = e / D, d = e - k * D;
-    if (mass[k] > 0.f) cent[(size_t)k * D4 + d] = sum[(size_t)k * D4 + d] / mass[k];
+// Weighted mean of each cluster from the points sorted by cluster: CTA k sums
+// its cluster's rows in a fixed order (4 interleaved row groups, combined in a
+// fixed tree), so the centroids do not depend on scheduling.  An empty cluster
+// keeps its centroid.
+__global__ void kmeans_segment_mean_kernel(const float *x, const float *w, int D, int D4, const int *perm,
+                                           const int *off, float *cent) {
+    __shared__ float ps[4][64];
+    __shared__ float pm[4];
+    const int k = blockIdx.x, t = threadIdx.x, d = t & 63, g = t >> 6;
+    const int a = off[k], b = off[k + 1];
+    float s = 0.f, m = 0.f;
+    for (int i = a + g; i < b; i += 4) {
+        const int src = perm[i];
+        const float wi = w ? w[src] : 1.f;
+        if (d < D) s = fmaf(wi, x[(size_t)src * D + d], s);
+        m += wi;
+    }
+    ps[g][d] = s;
+    if (d == 0) pm[g] = m;
+    __syncthreads();
+    if (g == 0 && d < D) {
+        const float S = (ps[0][d] + ps[1][d]) + (ps[2][d] + ps[3][d]);
+        const float M = (pm[0] + pm[1]) + (pm[2] + pm[3]);
+        if (M > 0.f) cent[(size_t)k * D4 + d] = S / M;
+    }
 }
 
 __global__ void gather_rows_kernel(const float *x, int D, const int *idx, int K, float *out, int D4) {
@@ -200,33 +210,31 @@ KmeansResult kmeans(otgb_ctx *ctx, const std::string &tag, const float *x, const
         OTGB_CHECK_LAUNCH();
         OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // idx is host memory about to go out of scope
     }
-    float *sum = ws.get<float>(tag + ":sum", (size_t)K * D4);
-    float *mass = ws.get<float>(tag + ":mass", K);
-    for (int it = 0; it < iters; ++it) {
-        kmeans_assign(x, n, D, r.centroids, K, r.labels, st);
-        OTGB_CUDA_TRY(cudaMemsetAsync(sum, 0, sizeof(float) * (size_t)K * D4, st));
-        OTGB_CUDA_TRY(cudaMemsetAsync(mass, 0, sizeof(float) * K, st));
-        kmeans_accum_kernel<<<n, 64, 0, st>>>(x, w, n, D, r.labels, sum, mass, D4);
-        OTGB_CHECK_LAUNCH();
-        kmeans_update_kernel<<<(K * D + 255) / 256, 256, 0, st>>>(r.centroids, sum, mass, K, D, D4);
-        OTGB_CHECK_LAUNCH();
-    }
-    kmeans_assign(x, n, D, r.centroids, K, r.labels, st);
     // stable sort by cluster and offsets of all K clusters (empty ones included)
     uint32_t *keys = ws.get<uint32_t>(tag + ":keys", n);
     int *counts = ws.get<int>(tag + ":cnt", K + 1);
     int *excl = ws.get<int>(tag + ":excl", K + 1);
-    OTGB_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (K + 1), st));
-    label_keys_kernel<<<(n + 255) / 256, 256, 0, st>>>(r.labels, n, keys, counts);
-    OTGB_CHECK_LAUNCH();
     int bits = 0;
     while ((1 << bits) < K) ++bits;
     void *scr = ws.get("sort:scratch", radix_sort_scratch_bytes(n));
-    radix_sort_pairs(keys, r.perm, n, bits, scr, st);
     int *sscr = ws.get<int>("scan:scratch", scan_scratch_ints(K + 1) + 64);
-    exclusive_scan(counts, excl, K, sscr, st);
-    offsets_finish_kernel<<<(K + 255) / 256, 256, 0, st>>>(excl, counts, K, r.offsets);
-    OTGB_CHECK_LAUNCH();
+    auto sort_by_label = [&]() {
+        OTGB_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (K + 1), st));
+        label_keys_kernel<<<(n + 255) / 256, 256, 0, st>>>(r.labels, n, keys, counts);
+        OTGB_CHECK_LAUNCH();
+        radix_sort_pairs(keys, r.perm, n, bits, scr, st);
+        exclusive_scan(counts, excl, K, sscr, st);
+        offsets_finish_kernel<<<(K + 255) / 256, 256, 0, st>>>(excl, counts, K, r.offsets);
+        OTGB_CHECK_LAUNCH();
+    };
+    for (int it = 0; it < iters; ++it) {
+        kmeans_assign(x, n, D, r.centroids, K, r.labels, st);
+        sort_by_label();
+        kmeans_segment_mean_kernel<<<K, 256, 0, st>>>(x, w, D, D4, r.perm, r.offsets, r.centroids);
+        OTGB_CHECK_LAUNCH();
+    }
+    kmeans_assign(x, n, D, r.centroids, K, r.labels, st);
+    sort_by_label();
     r.sorted_keys = keys;
     return r;
 }

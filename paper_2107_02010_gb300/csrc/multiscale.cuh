@@ -59,6 +59,8 @@ struct Solver {
     double softmin_ms = 0.0;
     long softmin_launches = 0;
     Multiscale *ms = nullptr;
+    bool g_from_f = false;                    // before the first step: g = one plain softmin of f
+    std::vector<std::vector<int>> work_ncols; // columns per (instance, block) of the current work
 
     ~Solver();
     void alloc_common();
@@ -72,6 +74,8 @@ struct Solver {
     std::string nm(const std::string &n) const { return tag + n; }
     void step(double sigma, bool count_pairs);
     void fine_step(double sigma);
+    // g~ of f alone (instance 2, no blend) at sigma, written into the current g
+    void sweep_g(double sigma);
     void harvest_timing();
     double divergence(double eps);
     int iterate_at_blur(const otgb_params &P, int it_budget);

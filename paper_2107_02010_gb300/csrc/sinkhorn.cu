@@ -237,6 +237,7 @@ void Solver::set_work(const std::vector<std::vector<int>> &ncols, bool allow_spl
             fin.push_back(make_int4(k, b, first, (int)items.size() - first));
         }
     const bool split = items.size() > fin.size();
+    work_ncols = ncols;
     int4 *d_items = ws->get<int4>(nm("items"), items.size() + 1);
     OTGB_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     launch.items = d_items;
@@ -382,7 +383,45 @@ int Solver::iterate_at_blur(const otgb_params &P, int it_budget) {
     }
 }
 
+// One sweep of the alpha -> beta instance with no old value: g_j = -lam eps
+// LSE_i(log alpha_i + (f_i - C(x_i, y_j)) / eps), over the kept columns of the
+// current work (all columns when dense).
+void Solver::sweep_g(double sigma) {
+    const double eps = sigma * sigma;
+    SoftminLaunch E = launch;
+    E.eps = (float)eps;
+    E.s = (float)(1.4426950408889634 / eps);
+    E.eps_ln2 = eps * 0.69314718055994530942;
+    SoftminInst &I = E.inst[2];
+    I.col_pot = pf[cur];
+    I.row_old = nullptr;
+    I.row_out = pg[cur];
+    I.lam = (float)lambda_of(sigma, reach);
+    I.omega = 1.0f;
+    require(work_ncols.size() == 4, "sweep_g: no work decomposition", OTGB_EINTERNAL);
+    std::vector<int4> items;
+    for (int bl = 0; bl < (int)work_ncols[2].size(); ++bl) items.push_back(make_int4(2, bl, 0, work_ncols[2][bl]));
+    int4 *d_items = ws->get<int4>(nm("gitems"), items.size() + 1);
+    OTGB_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    E.items = d_items;
+    E.n_items = (int)items.size();
+    E.part = nullptr;
+    E.fin = nullptr;
+    E.n_fin = 0;
+    E.delta_max = nullptr;
+    E.pairs = d_pairs;
+    softmin_run(E, D, rows_per_thread, st);
+    OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // the host item list goes out of scope
+    ++steps;
+}
+
 void Solver::fine_step(double sigma) {
+    if (g_from_f) {
+        g_from_f = false;
+        if (ms) ms->before_fine_step(*this, sigma);
+        sweep_g(sigma);
+        if (ms) ms->mask_sigma = -1.0;  // decide the kept pairs again with this g
+    }
     if (ms) ms->before_fine_step(*this, sigma);
     step(sigma, true);
     ++fine_steps;
@@ -491,6 +530,7 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
 
         s.alloc_common();
         s.alloc_pots(P);
+        s.g_from_f = P.init_g_from_f != 0 && P.f_init != nullptr && P.g_init == nullptr;
 
         // rows per CTA: enough CTAs to fill the GPU twice, else the smallest blocks
         // rows per thread (D <= 3): 4, so that one warp's block holds 128 rows

@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (t == 0 && tt + 1 < ntiles) issue(buf ^ 1);
         if (!mbar_wait(smem_u32(&S.mbar[buf]), phase[buf])) ok = false;
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
         phase[buf] ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (ok) {

@@ -47,6 +47,8 @@ class Params(C.Structure):
         ("translation", C.c_int),
         ("anderson", C.c_int),
         ("rows_per_thread", C.c_int),
+        ("init_g_from_f", C.c_int),
+        ("warm_max_iters", C.c_int),
     ]
 
 
@@ -68,6 +70,9 @@ class Stats(C.Structure):
         ("last_delta", C.c_double),
         ("last_rel_change", C.c_double),
         ("fallback_rows", C.c_longlong),
+        ("warm_start", C.c_int),
+        ("warm_iters", C.c_int),
+        ("warm_ms", C.c_double),
     ]
 
     def as_dict(self):
@@ -79,7 +84,11 @@ STATUS = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "ENOCONV", -5: "
 
 EXPORTS = ["otgb_default_params", "otgb_create", "otgb_destroy", "otgb_last_error", "sinkhorn_divergence",
            "transport_apply", "otgb_plan_free", "cluster_grid", "cluster_kmeans", "otgb_softmin",
-           "otgb_kernel_launches", "otgb_softmin_noalloc"]
+           "otgb_kernel_launches", "otgb_softmin_noalloc", "otgb_mlp_create", "otgb_mlp_destroy",
+           "otgb_mlp_n_params", "otgb_mlp_fit_normalization", "otgb_mlp_set_normalization",
+           "otgb_mlp_get_normalization", "otgb_mlp_set_params", "otgb_mlp_get_params", "otgb_mlp_grad",
+           "otgb_mlp_adam_step", "otgb_mlp_train_step", "otgb_mlp_train_epoch", "otgb_mlp_infer", "otgb_mlp_save",
+           "otgb_mlp_load", "sinkhorn_divergence_warm"]
 
 
 def kernel_launches() -> int:
@@ -125,8 +134,30 @@ def load(build_if_missing: bool = True):
     lib.otgb_softmin_noalloc.restype = ci
     lib.otgb_kernel_launches.argtypes = []
     lib.otgb_kernel_launches.restype = C.c_ulonglong
+    fp = C.POINTER(C.c_float)
+    lib.otgb_mlp_create.argtypes = [vp, ci, ci, C.c_ulonglong, C.POINTER(vp)]
+    lib.otgb_mlp_destroy.argtypes = [vp]
+    lib.otgb_mlp_n_params.argtypes = [vp]
+    lib.otgb_mlp_fit_normalization.argtypes = [vp, vp, vp, ci]
+    lib.otgb_mlp_set_normalization.argtypes = [vp, fp, fp, cd, cd]
+    lib.otgb_mlp_get_normalization.argtypes = [vp, fp, fp, C.POINTER(cd), C.POINTER(cd)]
+    lib.otgb_mlp_set_params.argtypes = [vp, fp, ci]
+    lib.otgb_mlp_get_params.argtypes = [vp, fp, ci]
+    lib.otgb_mlp_grad.argtypes = [vp, vp, vp, ci, C.POINTER(cd), vp]
+    lib.otgb_mlp_adam_step.argtypes = [vp, vp, C.c_float]
+    lib.otgb_mlp_train_step.argtypes = [vp, vp, vp, ci, C.c_float, C.POINTER(cd)]
+    lib.otgb_mlp_train_epoch.argtypes = [vp, vp, vp, ci, ci, C.c_float, C.c_ulonglong, C.POINTER(cd)]
+    lib.otgb_mlp_infer.argtypes = [vp, vp, ci, vp]
+    lib.otgb_mlp_save.argtypes = [vp, C.c_char_p]
+    lib.otgb_mlp_load.argtypes = [vp, C.c_char_p]
+    lib.sinkhorn_divergence_warm.argtypes = [vp, vp, vp, vp, ci, vp, vp, ci, ci, C.POINTER(Params), vp,
+                                             C.POINTER(cd), vp, vp, vp, vp, C.POINTER(vp), C.POINTER(Stats)]
     for name in ("otgb_create", "otgb_destroy", "sinkhorn_divergence", "transport_apply", "cluster_grid",
-                 "cluster_kmeans", "otgb_softmin"):
+                 "cluster_kmeans", "otgb_softmin", "otgb_mlp_create", "otgb_mlp_destroy", "otgb_mlp_n_params",
+                 "otgb_mlp_fit_normalization", "otgb_mlp_set_normalization", "otgb_mlp_get_normalization",
+                 "otgb_mlp_set_params", "otgb_mlp_get_params", "otgb_mlp_grad", "otgb_mlp_adam_step",
+                 "otgb_mlp_train_step", "otgb_mlp_train_epoch", "otgb_mlp_infer", "otgb_mlp_save", "otgb_mlp_load",
+                 "sinkhorn_divergence_warm"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -287,4 +318,117 @@ def softmin_noalloc(q, p, w, pot, eps, lam=1.0, old=None, omega=0.5, out=None, s
                                   C.c_void_p(st.cuda_stream))
     if rc != 0:
         raise OtgbError(rc, lib.otgb_last_error(None).decode())
+    return out
+
+
+class Mlp:
+    """The warm-start network of a context (otgb_mlp_*): D -> H -> H -> H -> 1."""
+
+    def __init__(self, ctx: Context, D: int, hidden: int = 256, seed: int = 0):
+        h = C.c_void_p()
+        ctx.check(load().otgb_mlp_create(ctx.h, int(D), int(hidden), int(seed), C.byref(h)))
+        self.ctx, self.h, self.D, self.H = ctx, h, int(D), int(hidden)
+        self.n_params = int(load().otgb_mlp_n_params(h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().otgb_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fit_normalization(self, x, f=None):
+        self.ctx.check(load().otgb_mlp_fit_normalization(self.h, _f32(x), _f32(f) if f is not None else None,
+                                                         x.shape[0]))
+
+    def set_normalization(self, in_mean, in_scale, out_mean, out_scale):
+        import numpy as np
+        m = np.ascontiguousarray(in_mean, dtype=np.float32)
+        s = np.ascontiguousarray(in_scale, dtype=np.float32)
+        fp = C.POINTER(C.c_float)
+        self.ctx.check(load().otgb_mlp_set_normalization(self.h, m.ctypes.data_as(fp), s.ctypes.data_as(fp),
+                                                         float(out_mean), float(out_scale)))
+
+    def get_normalization(self):
+        import numpy as np
+        m = np.zeros(self.D, np.float32)
+        s = np.zeros(self.D, np.float32)
+        om, os_ = C.c_double(), C.c_double()
+        fp = C.POINTER(C.c_float)
+        self.ctx.check(load().otgb_mlp_get_normalization(self.h, m.ctypes.data_as(fp), s.ctypes.data_as(fp),
+                                                         C.byref(om), C.byref(os_)))
+        return m, s, om.value, os_.value
+
+    def set_params(self, theta):
+        import numpy as np
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        self.ctx.check(load().otgb_mlp_set_params(self.h, t.ctypes.data_as(C.POINTER(C.c_float)), t.size))
+
+    def get_params(self):
+        import numpy as np
+        t = np.zeros(self.n_params, np.float32)
+        self.ctx.check(load().otgb_mlp_get_params(self.h, t.ctypes.data_as(C.POINTER(C.c_float)), t.size))
+        return t
+
+    def grad(self, x, f):
+        g = torch.empty(self.n_params, device=x.device, dtype=torch.float32)
+        loss = C.c_double()
+        self.ctx.check(load().otgb_mlp_grad(self.h, _f32(x), _f32(f), x.shape[0], C.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def adam_step(self, grad, lr):
+        self.ctx.check(load().otgb_mlp_adam_step(self.h, _f32(grad), float(lr)))
+
+    def train_step(self, x, f, lr):
+        loss = C.c_double()
+        self.ctx.check(load().otgb_mlp_train_step(self.h, _f32(x), _f32(f), x.shape[0], float(lr), C.byref(loss)))
+        return loss.value
+
+    def train_epoch(self, x, f, batch, lr, seed):
+        loss = C.c_double()
+        self.ctx.check(load().otgb_mlp_train_epoch(self.h, _f32(x), _f32(f), x.shape[0], int(batch), float(lr),
+                                                   int(seed), C.byref(loss)))
+        return loss.value
+
+    def infer(self, x):
+        out = torch.empty(x.shape[0], device=x.device, dtype=torch.float32)
+        self.ctx.check(load().otgb_mlp_infer(self.h, _f32(x), x.shape[0], _ptr(out)))
+        return out
+
+    def save(self, path):
+        self.ctx.check(load().otgb_mlp_save(self.h, str(path).encode()))
+
+    def load_file(self, path):
+        self.ctx.check(load().otgb_mlp_load(self.h, str(path).encode()))
+
+
+def sinkhorn_divergence_warm(ctx: Context, mlp: Mlp, x, a, y, b, params: Params | None = None, b_atlas=None,
+                             want_self=False, want_plan=False, raise_on_noconv=True):
+    """Warm-started solve (sinkhorn_divergence_warm); returns the dict of
+    sinkhorn_divergence with stats (stats["warm_start"]: 1 warm, 2 fell back)."""
+    N, D = x.shape
+    M = y.shape[0]
+    f = torch.empty(N, device=x.device, dtype=torch.float32)
+    g = torch.empty(M, device=x.device, dtype=torch.float32)
+    aa = torch.empty(N, device=x.device, dtype=torch.float32) if want_self else None
+    bb = torch.empty(M, device=x.device, dtype=torch.float32) if want_self else None
+    cost = C.c_double()
+    plan = C.c_void_p() if want_plan else None
+    st = Stats()
+    p = params if params is not None else default_params()
+    rc = load().sinkhorn_divergence_warm(ctx.h, mlp.h, _f32(x), _f32(a), N, _f32(y), _f32(b), M, D, C.byref(p),
+                                         _f32(b_atlas) if b_atlas is not None else None, C.byref(cost), _ptr(f),
+                                         _ptr(g), _ptr(aa), _ptr(bb), C.byref(plan) if plan is not None else None,
+                                         C.byref(st))
+    if rc != 0 and not (rc == -4 and not raise_on_noconv):
+        ctx.check(rc)
+    out = dict(S=cost.value, f=f, g=g, status=rc, stats=st.as_dict())
+    if want_self:
+        out["a_self"], out["b_self"] = aa, bb
+    if want_plan:
+        out["plan"] = Plan(plan, (x, y, b))
     return out
