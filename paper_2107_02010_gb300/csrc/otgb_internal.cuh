@@ -141,6 +141,7 @@ struct SoftminLaunch {
     unsigned int *delta_max; // max |new - old| / eps as float bits (non-negative); may be null
     int4 *fallback;          // (instance, row, block, 0) of rows needing the safe path
     int *n_fallback;
+    int *work_counter;       // D <= 3 kernel: non-null = warps pull items from this counter (zeroed per launch)
     int fallback_cap;
     unsigned long long *fallback_total; // running count of fallback rows (may be null)
     unsigned long long *pairs; // evaluated pair counter (may be null)

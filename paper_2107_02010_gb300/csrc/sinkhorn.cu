@@ -261,6 +261,7 @@ void Solver::alloc_common() {
     const int cap = 2 * (X.n + Y.n) + 64;
     launch.fallback = ws->get<int4>(nm("fb"), cap);
     launch.n_fallback = ws->get<int>(nm("nfb"), 1);
+    launch.work_counter = ws->get<int>(nm("wctr"), 1);
     launch.fallback_cap = cap;
     d_fb_total = ws->get<unsigned long long>(nm("fbtot"), 1);
     launch.fallback_total = d_fb_total;

@@ -102,8 +102,17 @@ __device__ __forceinline__ void push_fallback(const SoftminLaunch &L, int inst, 
 // stages 32 columns per tile as (Y0,Y0,Y1,Y1 | Y2,Y2,H,H), double buffered, so
 // that one 16-byte shared load feeds a packed operand pair.  TWO = true: an
 // exact-maximum first pass gives each row's shift (no old value).
-constexpr int kW3 = 4;    // warps per CTA
-constexpr int kT3 = 128;  // columns per warp tile (4 staged per lane)
+// Tile width and resident CTAs per SM: 128 columns and 6 CTAs (80 registers)
+// measured fastest on the track-density workload among 32/64/128 columns and
+// 5-8 CTAs (the occupancy changes the step time by under 5 %).
+#ifndef OTGB_SM3_TILE
+#define OTGB_SM3_TILE 128
+#endif
+#ifndef OTGB_SM3_MINB
+#define OTGB_SM3_MINB 6
+#endif
+constexpr int kW3 = 4;               // warps per CTA
+constexpr int kT3 = OTGB_SM3_TILE;   // columns per warp tile (kT3 / 32 staged per lane)
 constexpr int kCPL = kT3 / 32;
 
 __device__ __forceinline__ bool row_sum_ok(float a) { return a >= 0x1p-60f && a <= 0x1p60f; }
@@ -155,11 +164,15 @@ __device__ __forceinline__ void setup_rows3(const SoftminLaunch &L, const Softmi
 }
 
 // Finish the R rows of this lane from their sums: flag, log, blend, write.
+// The translated row point is recomputed from the packed rows (the same float
+// subtraction as in setup_rows3, hence the same value), so that the row
+// coordinates need not stay in registers through the column loop.
 template <int R>
 __device__ __forceinline__ void finish_rows3(const SoftminLaunch &L, const SoftminInst &I, int inst, int blk, int r0,
-                                             int r1, const float (&xr)[R][3], const float (&m)[R],
+                                             int r1, const float (&c)[3], const float (&m)[R],
                                              const float (&tot)[R]) {
     const int lane = threadIdx.x & 31;
+    const float4 *rows4 = reinterpret_cast<const float4 *>(I.rows);
     float dmax = 0.f;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
@@ -170,22 +183,20 @@ __device__ __forceinline__ void finish_rows3(const SoftminLaunch &L, const Softm
             push_fallback(L, inst, r, blk);
             continue;
         }
-        const double hx = 0.5 * ((double)xr[k][0] * xr[k][0] + (double)xr[k][1] * xr[k][1] +
-                                 (double)xr[k][2] * xr[k][2]);
+        const float4 p = rows4[r];
+        const float x0 = p.x - c[0], x1 = p.y - c[1], x2 = p.z - c[2];
+        const double hx = 0.5 * ((double)x0 * x0 + (double)x1 * x1 + (double)x2 * x2);
         finish_row(L, I, r, (double)m[k] + log2((double)a), hx, dmax);
     }
     dmax = warp_max(dmax);
     if (lane == 0 && L.delta_max) atomicMax(L.delta_max, __float_as_uint(dmax));
 }
 
+// One work item of the D <= 3 sweep, computed by one warp in its shared-memory
+// slice `tile`.
 template <int R, bool TWO>
-__global__ void __launch_bounds__(32 * kW3, 5) softmin3_kernel(const __grid_constant__ SoftminLaunch L) {
-    __shared__ __align__(16) float4 tiles[kW3][2][kT3][2];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int it = blockIdx.x * kW3 + warp;
-    if (it >= L.n_items) return;  // whole warp: no CTA-wide barrier follows
-    float4 (*tile)[kT3][2] = tiles[warp];
-
+__device__ __forceinline__ void softmin3_item(const SoftminLaunch &L, int it, float4 (*tile)[kT3][2]) {
+    const int lane = threadIdx.x & 31;
     int4 item = L.items[it];
     OTGB_DCLAMP(item.x, 0, L.n_inst);
     const SoftminInst &I = L.inst[item.x];
@@ -209,16 +220,28 @@ __global__ void __launch_bounds__(32 * kW3, 5) softmin3_kernel(const __grid_cons
     const int ncol = ce - cb;
     const int ntiles = (ncol + kT3 - 1) / kT3;
 
-    // staging of one tile: lane l loads columns p0 + l + 32 u, u < kCPL
-    auto load_col = [&](int p0, float4 (&q)[kCPL], float (&pot)[kCPL]) {
+    // staging of one tile: lane l handles columns p0 + l + 32 u, u < kCPL.  The
+    // column indices are fetched one tile ahead of the column data, so that the
+    // list -> point dependency of a tile is resolved while the tile before it
+    // is computed.
+    auto load_idx = [&](int p0, int (&j)[kCPL]) {
 #pragma unroll
         for (int u = 0; u < kCPL; ++u) {
             const int p = p0 + lane + 32 * u;
+            int jj = -1;
             if (p < ncol) {
-                int j = list ? list[c0 + cb + p] : cb + p;
-                OTGB_DCLAMP(j, 0, I.n_cols);
-                q[u] = cols4[j];
-                pot[u] = I.col_pot[j];
+                jj = list ? list[c0 + cb + p] : cb + p;
+                OTGB_DCLAMP(jj, 0, I.n_cols);
+            }
+            j[u] = jj;
+        }
+    };
+    auto load_col = [&](const int (&j)[kCPL], float4 (&q)[kCPL], float (&pot)[kCPL]) {
+#pragma unroll
+        for (int u = 0; u < kCPL; ++u) {
+            if (j[u] >= 0) {
+                q[u] = cols4[j[u]];
+                pot[u] = I.col_pot[j[u]];
             } else {
                 q[u] = make_float4(0.f, 0.f, 0.f, -INFINITY);
                 pot[u] = 0.f;
@@ -253,12 +276,17 @@ __global__ void __launch_bounds__(32 * kW3, 5) softmin3_kernel(const __grid_cons
         float mx[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) mx[k] = -INFINITY;
-        if (ntiles > 0) { load_col(0, q, pot); store_col(0, q, pot); }
+        int jn[kCPL];
+        if (ntiles > 0) { load_idx(0, jn); load_col(jn, q, pot); store_col(0, q, pot); }
+        if (ntiles > 1) load_idx(kT3, jn);
         __syncwarp();
         for (int tt = 0; tt < ntiles; ++tt) {
             const int buf = tt & 1;
             const bool more = tt + 1 < ntiles;
-            if (more) load_col((tt + 1) * kT3, q, pot);
+            if (more) {
+                load_col(jn, q, pot);
+                if (tt + 2 < ntiles) load_idx((tt + 2) * kT3, jn);
+            }
             const int n = min(kT3, ncol - tt * kT3);
             for (int cc = 0; cc < n; ++cc) {
                 const float4 a = tile[buf][cc][0], b = tile[buf][cc][1];
@@ -284,12 +312,17 @@ __global__ void __launch_bounds__(32 * kW3, 5) softmin3_kernel(const __grid_cons
 #pragma unroll
     for (int p = 0; p < P; ++p) Mn[p] = pack2(-m[2 * p], -m[2 * p + 1]);
 
-    if (ntiles > 0) { load_col(0, q, pot); store_col(0, q, pot); }
+    int jn[kCPL];
+    if (ntiles > 0) { load_idx(0, jn); load_col(jn, q, pot); store_col(0, q, pot); }
+    if (ntiles > 1) load_idx(kT3, jn);
     __syncwarp();
     for (int tt = 0; tt < ntiles; ++tt) {
         const int buf = tt & 1;
         const bool more = tt + 1 < ntiles;
-        if (more) load_col((tt + 1) * kT3, q, pot);
+        if (more) {
+            load_col(jn, q, pot);
+            if (tt + 2 < ntiles) load_idx((tt + 2) * kT3, jn);
+        }
         int n = min(kT3, ncol - tt * kT3);
         n = (n + 3) & ~3;  // padded columns carry H = -inf
         if constexpr (R >= 2) {
@@ -347,9 +380,43 @@ __global__ void __launch_bounds__(32 * kW3, 5) softmin3_kernel(const __grid_cons
         // split block: partial sums, finished by softmin3_finalize_kernel
 #pragma unroll
         for (int k = 0; k < R; ++k) L.part[(size_t)it * kPartRows + lane + 32 * k] = tot[k];
+    } else {
+        if constexpr (R >= 2) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                float lo, hi;
+                unpack2(Mn[p], lo, hi);
+                m[2 * p] = -lo;
+                m[2 * p + 1] = -hi;
+            }
+        }
+        finish_rows3<R>(L, I, item.x, blk, r0, r1, c, m, tot);
+    }
+}
+
+// Warps take work items in order: statically (item = global warp index) or,
+// when L.work_counter is set, from the counter until none is left, so that no
+// warp idles while a slow item of its CTA finishes and the grid can be sized
+// to the resident capacity.  Every item writes only its own rows or partial
+// sums, so the result does not depend on which warp computed it.
+template <int R, bool TWO>
+__global__ void __launch_bounds__(32 * kW3, OTGB_SM3_MINB) softmin3_kernel(const __grid_constant__ SoftminLaunch L) {
+    __shared__ __align__(16) float4 tiles[kW3][2][kT3][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 (*tile)[kT3][2] = tiles[warp];
+    if (!L.work_counter) {
+        const int it = blockIdx.x * kW3 + warp;
+        if (it < L.n_items) softmin3_item<R, TWO>(L, it, tile);
         return;
     }
-    finish_rows3<R>(L, I, item.x, blk, r0, r1, xr, m, tot);
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(L.work_counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= L.n_items) return;  // whole warp: no CTA-wide barrier in this kernel
+        softmin3_item<R, TWO>(L, it, tile);
+        __syncwarp();
+    }
 }
 
 // Split blocks: one warp per block sums the partial sums of its items in item
@@ -378,7 +445,7 @@ __global__ void __launch_bounds__(32 * kW3) softmin3_finalize_kernel(const __gri
 #pragma unroll
         for (int k = 0; k < R; ++k) tot[k] += L.part[(size_t)item * kPartRows + lane + 32 * k];
     }
-    finish_rows3<R>(L, I, fe.x, blk, r0, r1, xr, m, tot);
+    finish_rows3<R>(L, I, fe.x, blk, r0, r1, c, m, tot);
 }
 
 // ------------------------------------------------------------ 3 < D <= 64 --
@@ -636,6 +703,30 @@ int uniform_blocks(int *d_blk_row0, int n, int block_rows, cudaStream_t st) {
     return nb;
 }
 
+namespace {
+
+// Grid of the D <= 3 kernel: one warp per item, or, with a work counter, at most
+// the CTAs that fit on the GPU at once (each warp then takes items until none
+// is left).
+template <int R, bool TWO>
+void launch_softmin3(const SoftminLaunch &L, cudaStream_t st) {
+    int grid = (L.n_items + kW3 - 1) / kW3;
+    if (L.work_counter) {
+        static int cap = 0;
+        if (!cap) {
+            int dev = 0, sms = 0, occ = 0;
+            OTGB_CUDA_TRY(cudaGetDevice(&dev));
+            OTGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            OTGB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, softmin3_kernel<R, TWO>, 32 * kW3, 0));
+            cap = sms * (occ > 0 ? occ : 1);
+        }
+        grid = grid < cap ? grid : cap;
+    }
+    softmin3_kernel<R, TWO><<<grid, 32 * kW3, 0, st>>>(L);
+}
+
+}  // namespace
+
 void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_t st) {
     if (L.n_items <= 0) return;
     OTGB_CUDA_TRY(cudaMemsetAsync(L.n_fallback, 0, sizeof(int), st));
@@ -645,14 +736,14 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
     require(!(two && L.part), "softmin_run: split blocks need old values", OTGB_EINTERNAL);
     require(!(D > 3 && L.part), "softmin_run: split blocks are D <= 3 only", OTGB_EINTERNAL);
     if (D <= 3) {
-        const int grid = (L.n_items + kW3 - 1) / kW3;
+        if (L.work_counter) OTGB_CUDA_TRY(cudaMemsetAsync(L.work_counter, 0, sizeof(int), st));
         switch (rows_per_thread + (two ? 8 : 0)) {
-            case 1: softmin3_kernel<1, false><<<grid, 32 * kW3, 0, st>>>(L); break;
-            case 2: softmin3_kernel<2, false><<<grid, 32 * kW3, 0, st>>>(L); break;
-            case 4: softmin3_kernel<4, false><<<grid, 32 * kW3, 0, st>>>(L); break;
-            case 9: softmin3_kernel<1, true><<<grid, 32 * kW3, 0, st>>>(L); break;
-            case 10: softmin3_kernel<2, true><<<grid, 32 * kW3, 0, st>>>(L); break;
-            default: softmin3_kernel<4, true><<<grid, 32 * kW3, 0, st>>>(L); break;
+            case 1: launch_softmin3<1, false>(L, st); break;
+            case 2: launch_softmin3<2, false>(L, st); break;
+            case 4: launch_softmin3<4, false>(L, st); break;
+            case 9: launch_softmin3<1, true>(L, st); break;
+            case 10: launch_softmin3<2, true>(L, st); break;
+            default: launch_softmin3<4, true>(L, st); break;
         }
         OTGB_CHECK_LAUNCH();
         if (L.part && L.n_fin > 0) {
