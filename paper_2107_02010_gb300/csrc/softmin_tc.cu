@@ -166,43 +166,71 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
     const int ncol = ce - cb;
     const int ntiles = (ncol + kTcN - 1) / kTcN;
 
-    auto stage = [&](int tile, int buf) {
+    // Staging of a column tile, software-pipelined over three tiles: the
+    // column indices of tile t+3 and the raw coordinates of tile t+2 are
+    // loaded into registers while the tensor core multiplies tile t+1 and the
+    // CTA finishes tile t, so no load latency sits between two tiles.  Thread
+    // t handles chunk ch = t % 8 (coordinates 8 ch .. 8 ch + 7) of the columns
+    // t / 8 + 16 k, k < 8; the 8 threads of a column sum its |yt|^2.
+    constexpr int kU = kTcN * 8 / 128;
+    const int ch = t & 7, colb = t >> 3;
+    int jc[kU], jn[kU];
+    float4 ra[kU], rb[kU];
+    float rlw[kU], rpot[kU];
+    auto load_idx = [&](int tile, int (&j)[kU]) {
         const int p0 = tile * kTcN;
-        for (int u = t; u < kTcN * 8; u += 128) {
-            const int col = u >> 3, ch = u & 7;
-            const int p = p0 + col;
-            float v[8];
-            int j = -1;
-            if (p < ncol) {
-                j = list ? list[c0 + cb + p] : cb + p;
-                OTGB_DCLAMP(j, 0, I.n_cols);
-            }
-            if (j >= 0 && ch * 8 + 8 <= D4) {
-                const float4 a = *reinterpret_cast<const float4 *>(I.cols + (size_t)j * D4 + ch * 8);
-                const float4 b = *reinterpret_cast<const float4 *>(I.cols + (size_t)j * D4 + ch * 8 + 4);
-                v[0] = a.x - S.cen[ch * 8]; v[1] = a.y - S.cen[ch * 8 + 1]; v[2] = a.z - S.cen[ch * 8 + 2];
-                v[3] = a.w - S.cen[ch * 8 + 3]; v[4] = b.x - S.cen[ch * 8 + 4]; v[5] = b.y - S.cen[ch * 8 + 5];
-                v[6] = b.z - S.cen[ch * 8 + 6]; v[7] = b.w - S.cen[ch * 8 + 7];
-            } else {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int k = ch * 8 + e;
-                    v[e] = (j >= 0 && k < D4) ? I.cols[(size_t)j * D4 + k] - S.cen[k] : 0.f;
+        for (int k = 0; k < kU; ++k) {
+            const int p = p0 + colb + 16 * k;
+            int jj = -1;
+            if (tile < ntiles && p < ncol) {
+                jj = list ? list[c0 + cb + p] : cb + p;
+                OTGB_DCLAMP(jj, 0, I.n_cols);
+            }
+            j[k] = jj;
+        }
+    };
+    auto load_raw = [&]() {
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int jj = jc[k];
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            float lw = 0.f, pt = 0.f;
+            if (jj >= 0) {
+                const float *src = I.cols + (size_t)jj * D4 + ch * 8;
+                if (ch * 8 + 4 <= D4) a = *reinterpret_cast<const float4 *>(src);
+                if (ch * 8 + 8 <= D4) b = *reinterpret_cast<const float4 *>(src + 4);
+                if (ch == 0) {
+                    lw = I.col_logw[jj];
+                    pt = I.col_pot[jj];
                 }
             }
+            ra[k] = a;
+            rb[k] = b;
+            rlw[k] = lw;
+            rpot[k] = pt;
+        }
+    };
+    auto convert = [&](int buf) {
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int col = colb + 16 * k;
+            const bool ok_col = jc[k] >= 0;
+            const float *cn = S.cen + ch * 8;
+            float v[8] = {ra[k].x - cn[0], ra[k].y - cn[1], ra[k].z - cn[2], ra[k].w - cn[3],
+                          rb[k].x - cn[4], rb[k].y - cn[5], rb[k].z - cn[6], rb[k].w - cn[7]};
             float sq = 0.f;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) sq = fmaf(v[e], v[e], sq);
+            for (int e = 0; e < 8; ++e) {
+                v[e] = ok_col ? v[e] : 0.f;
+                sq = fmaf(v[e], v[e], sq);
+            }
             uint4 hi, lo;
             split8(v, hi, lo);
             *reinterpret_cast<uint4 *>(S.b_hi[buf] + core_off(col, ch * 8)) = hi;
             *reinterpret_cast<uint4 *>(S.b_lo[buf] + core_off(col, ch * 8)) = lo;
             for (int o = 4; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            if (ch == 0) {
-                float H = -INFINITY;
-                if (j >= 0) H = s * (fmaf(eps, I.col_logw[j], I.col_pot[j]) - 0.5f * sq);
-                S.h[buf][col] = H;
-            }
+            if (ch == 0) S.h[buf][col] = ok_col ? s * (fmaf(eps, rlw[k], rpot[k]) - 0.5f * sq) : -INFINITY;
         }
     };
 
@@ -244,7 +272,14 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
     float tot = 0.f;
     uint32_t phase[2] = {0u, 0u};
     bool ok = true;
-    if (ntiles > 0) stage(0, 0);
+    if (ntiles > 0) {
+        load_idx(0, jc);
+        load_raw();
+        convert(0);
+        load_idx(1, jc);
+        load_raw();
+        load_idx(2, jn);
+    }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -252,7 +287,13 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
     if (t == 0 && ntiles > 0) issue(0);
     for (int tt = 0; tt < ntiles; ++tt) {
         const int buf = tt & 1;
-        if (tt + 1 < ntiles) stage(tt + 1, buf ^ 1);
+        if (tt + 1 < ntiles) {
+            convert(buf ^ 1);  // tile tt+1 from registers
+#pragma unroll
+            for (int k = 0; k < kU; ++k) jc[k] = jn[k];
+            load_raw();             // tile tt+2 (nothing past the end)
+            load_idx(tt + 3, jn);   // indices of tile tt+3
+        }
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
