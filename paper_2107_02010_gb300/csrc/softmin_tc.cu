@@ -39,6 +39,7 @@ struct TcSmem {
     unsigned char b_lo[2][kTileBytes];
     float h[2][kTcN];
     float cen[64];
+    float red[4];
     unsigned long long mbar[2];
     uint32_t tslot;
 };
@@ -100,6 +101,14 @@ __device__ __forceinline__ void finish_row_tc(const SoftminLaunch &L, const Soft
     I.row_out[r] = (float)nw;
 }
 
+// FOLD (D4 <= 60): the free K slots 60..63 carry the rest of the exponent, so
+// that the accumulator holds H_j - m_i + s xt_i . yt_j and the epilogue is
+// just ex2 and a sum: column slots 60-62 hold H_j as three BF16 pieces (about
+// 24 significant bits) against 1.0 in the row operand, row slot 63 holds the
+// row shift rounded to BF16 against 1.0 in the column operand.  Any shift is
+// valid as long as the finish adds back the same value, so the rounded shift
+// costs nothing in accuracy.
+template <bool FOLD>
 __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constant__ SoftminLaunch L, int D4) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
@@ -140,6 +149,10 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
         for (int e = 0; e < 8; ++e) { sq = fmaf(v[e], v[e], sq); v[e] *= s; }
         uint4 hi, lo;
         split8(v, hi, lo);
+        if (FOLD && ch == 7) {  // slots 60, 61, 62 = 1.0 (the H pieces); 63 = the shift, written below
+            hi.z = 0x3F803F80u;
+            hi.w = 0x00003F80u;
+        }
         *reinterpret_cast<uint4 *>(S.a_hi + core_off(r, ch * 8)) = hi;
         *reinterpret_cast<uint4 *>(S.a_lo + core_off(r, ch * 8)) = lo;
         // |xt|^2 of row r: sum over its 8 chunks (8 consecutive lanes)
@@ -154,6 +167,22 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
     const double hx = 0.5 * (double)x2;
     float m = 0.f;
     if (valid) m = (float)((double)s * (hx - (double)I.row_old[r0 + myr] / (double)I.lam));
+    // FOLD: a block constant C (the largest row shift) is taken out of both
+    // folded terms, so that the accumulator adds H_j - C and -(m_i - C), small
+    // for every pair that matters, instead of two large values that cancel.
+    float Cb = 0.f;
+    double m_eff = (double)m;  // the row shift the finish adds back
+    if (FOLD) {
+        float mx = valid ? m : -INFINITY;
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) S.red[warp] = mx;
+        __syncthreads();
+        Cb = fmaxf(fmaxf(S.red[0], S.red[1]), fmaxf(S.red[2], S.red[3]));
+        if (!(Cb > -INFINITY)) Cb = 0.f;
+        const __nv_bfloat16 mb = __float2bfloat16_rn(-(m - Cb));
+        m_eff = (double)Cb - (double)__bfloat162float(mb);  // the shift the accumulator applies
+        *reinterpret_cast<__nv_bfloat16 *>(S.a_hi + core_off(myr, 63)) = mb;
+    }
     __syncthreads();  // S.h[0] is reused for the columns
 
     // ---- columns of this item
@@ -200,7 +229,7 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
                 const float *src = I.cols + (size_t)jj * D4 + ch * 8;
                 if (ch * 8 + 4 <= D4) a = *reinterpret_cast<const float4 *>(src);
                 if (ch * 8 + 8 <= D4) b = *reinterpret_cast<const float4 *>(src + 4);
-                if (ch == 0) {
+                if (ch == (FOLD ? 7 : 0)) {
                     lw = I.col_logw[jj];
                     pt = I.col_pot[jj];
                 }
@@ -227,10 +256,24 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
             }
             uint4 hi, lo;
             split8(v, hi, lo);
+            for (int o = 4; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if (FOLD) {
+                if (ch == 7) {  // slots 60-62: H in three BF16 pieces; 63: 1.0 against the row shift
+                    const float H = ok_col ? s * (fmaf(eps, rlw[k], rpot[k]) - 0.5f * sq) - Cb : -1e30f;
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(H);
+                    const float r1 = H - __bfloat162float(h1);
+                    const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
+                    const __nv_bfloat16 h3 = __float2bfloat16_rn(r1 - __bfloat162float(h2));
+                    hi.z = (uint32_t)__bfloat16_as_ushort(h1) | ((uint32_t)__bfloat16_as_ushort(h2) << 16);
+                    hi.w = (uint32_t)__bfloat16_as_ushort(h3) | (0x3F80u << 16);
+                    lo.z = 0u;
+                    lo.w = 0u;
+                }
+            } else if (ch == 0) {
+                S.h[buf][col] = ok_col ? s * (fmaf(eps, rlw[k], rpot[k]) - 0.5f * sq) : -INFINITY;
+            }
             *reinterpret_cast<uint4 *>(S.b_hi[buf] + core_off(col, ch * 8)) = hi;
             *reinterpret_cast<uint4 *>(S.b_lo[buf] + core_off(col, ch * 8)) = lo;
-            for (int o = 4; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            if (ch == 0) S.h[buf][col] = ok_col ? s * (fmaf(eps, rlw[k], rpot[k]) - 0.5f * sq) : -INFINITY;
         }
     };
 
@@ -319,12 +362,24 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
                     : "r"(a));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 float a0 = 0.f, a1 = 0.f;
+                if (FOLD) {
+                    float a2 = 0.f, a3 = 0.f;
 #pragma unroll
-                for (int q = 0; q < 32; q += 2) {
-                    a0 += ex2(__uint_as_float(v[q]) + (S.h[buf][c + q] - m));
-                    a1 += ex2(__uint_as_float(v[q + 1]) + (S.h[buf][c + q + 1] - m));
+                    for (int q = 0; q < 32; q += 4) {
+                        a0 += ex2(__uint_as_float(v[q]));
+                        a1 += ex2(__uint_as_float(v[q + 1]));
+                        a2 += ex2(__uint_as_float(v[q + 2]));
+                        a3 += ex2(__uint_as_float(v[q + 3]));
+                    }
+                    tot += (a0 + a1) + (a2 + a3);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; q += 2) {
+                        a0 += ex2(__uint_as_float(v[q]) + (S.h[buf][c + q] - m));
+                        a1 += ex2(__uint_as_float(v[q + 1]) + (S.h[buf][c + q + 1] - m));
+                    }
+                    tot += a0 + a1;
                 }
-                tot += a0 + a1;
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -344,7 +399,7 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
             const int k = atomicAdd(L.n_fallback, 1);
             if (k < L.fallback_cap) L.fallback[k] = make_int4(item.x, r, blk, 0);
         } else {
-            finish_row_tc(L, I, r, (double)m + log2((double)tot), hx, dmax);
+            finish_row_tc(L, I, r, m_eff + log2((double)tot), hx, dmax);
         }
     }
     for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -359,11 +414,14 @@ void softmin_tc_launch(const SoftminLaunch &L, int D, cudaStream_t st) {
     const int D4 = (D + 3) & ~3;
     static bool attr = false;
     if (!attr) {
-        OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)softmin_tc_smem_bytes()));
+        OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)softmin_tc_smem_bytes()));
         attr = true;
     }
-    softmin_tc_kernel<<<L.n_items, 128, softmin_tc_smem_bytes(), st>>>(L, D4);
+    if (D4 <= 60) softmin_tc_kernel<true><<<L.n_items, 128, softmin_tc_smem_bytes(), st>>>(L, D4);
+    else softmin_tc_kernel<false><<<L.n_items, 128, softmin_tc_smem_bytes(), st>>>(L, D4);
     OTGB_CHECK_LAUNCH();
 }
 
