@@ -81,6 +81,7 @@ struct Solver {
     int iterate_at_blur(const otgb_params &P, int it_budget);
     static bool converged(const std::vector<double> &hist, double tol, double floor_abs, double *rem_out);
     int no_progress = 0;
+    int floor_hits = 0;
     double delta_best = 1e300;
     bool potentials_converged(double delta_prev, double delta, int m, double eps, double potmax, double tol);
 };

@@ -311,8 +311,10 @@ void Solver::alloc_pots(const otgb_params &P) {
 // S can settle long before the potentials (it is insensitive to the slow
 // translation mode (f + c, g - c)), so both tails must be small:
 //   S tail <= tol |S| + floor,   potential tail <= max(tol, 1e-6) (max|pot| + eps).
-// A potential increment that no longer contracts but sits at the float32
-// rounding level (<= 4e-7 (max|pot| + eps)) counts as converged.
+// At the float32 floor the step no longer contracts: two checks in a row
+// whose step is at most two units in the last place of the largest dual, or
+// three checks without a new smallest step while the step is below
+// 1e-5 (max|pot| + eps), count as converged.
 bool Solver::converged(const std::vector<double> &hist, double tol, double floor_abs, double *rem_out) {
     const size_t k = hist.size();
     if (k < 3) return false;
@@ -344,6 +346,13 @@ bool Solver::potentials_converged(double delta_prev, double delta, int m, double
     }
     const double r = std::pow(delta / delta_prev, 1.0 / m);
     if (r < 0.999 && delta * eps * r / (1.0 - r) <= tol_pot) return true;  // geometric tail
+    // the float32 floor: a step of at most two units in the last place of the
+    // largest dual can only move the duals by rounding, so two such windows in a
+    // row end the loop
+    const float pm = (float)potmax;
+    const double ulp = (double)(std::nextafter(pm, INFINITY) - pm);
+    floor_hits = (delta * eps <= 2.0 * ulp) ? floor_hits + 1 : 0;
+    if (floor_hits >= 2) return true;
     // three windows without a new smallest step: the float32 rounding floor of
     // the duals; accept when the step itself is small
     return no_progress >= 3 && delta * eps <= 1e-5 * scale;
