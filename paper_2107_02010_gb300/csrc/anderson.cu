@@ -21,7 +21,7 @@ namespace otgb {
 namespace {
 
 constexpr int kAT = 256;
-constexpr int kAB = 120;  // CTAs of the dot-product pass
+constexpr int kAB = 456;  // CTAs of the dot-product pass (3 per SM on 152 SMs)
 
 // Store G_k and r_k = G_k - z_k in ring slot `slot`; partial dot products
 // <r_k, r_s> for every slot s (the slots not yet filled give garbage that the
@@ -32,9 +32,10 @@ __global__ void aa_dots_kernel(const float *z, const float *G, int n, float *Rri
     const int slot = state[0];
     float *rs = Rring + (size_t)slot * n;
     float *gs = Gring + (size_t)slot * n;
-    double acc[kAAMax + 1];
+    // a thread sums its few elements in float; double from the warp sums on
+    float acc[kAAMax + 1];
 #pragma unroll
-    for (int s = 0; s <= kAAMax; ++s) acc[s] = 0.0;
+    for (int s = 0; s <= kAAMax; ++s) acc[s] = 0.f;
     for (int i = blockIdx.x * kAT + threadIdx.x; i < n; i += gridDim.x * kAT) {
         const float g = G[i];
         const float r = g - z[i];
@@ -42,12 +43,12 @@ __global__ void aa_dots_kernel(const float *z, const float *G, int n, float *Rri
         gs[i] = g;
 #pragma unroll
         for (int s = 0; s <= kAAMax; ++s)
-            if (s < slots) acc[s] += (double)r * (double)(s == slot ? r : Rring[(size_t)s * n + i]);
+            if (s < slots) acc[s] = fmaf(r, s == slot ? r : Rring[(size_t)s * n + i], acc[s]);
     }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
     for (int s = 0; s <= kAAMax; ++s) {
-        double v = acc[s];
+        double v = (double)acc[s];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (l == 0) red[w][s] = v;
     }
@@ -66,16 +67,22 @@ __global__ void aa_dots_kernel(const float *z, const float *G, int n, float *Rri
 // z_{k+1} = sum_s coef[s] G_s.
 __global__ void aa_solve_kernel(const double *part, int nblk, int slots, int m, double reg, int *state, double *Q,
                                 double *best, double *coef) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    // the block partials: lane l sums blocks l, l + 32, ... (fixed order), then the warp
+    const int lane = threadIdx.x;
+    double d[kAAMax + 1];
+#pragma unroll
+    for (int s = 0; s <= kAAMax; ++s) {
+        double v = 0.0;
+        if (s < slots)
+            for (int b = lane; b < nblk; b += 32) v += part[(size_t)b * (kAAMax + 1) + s];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        d[s] = v;
+    }
+    if (lane != 0) return;
     const int slot = state[0];
     int cnt = state[1] + 1;
     if (cnt > slots) cnt = slots;
-    double d[kAAMax + 1];
-    for (int s = 0; s < slots; ++s) {
-        double v = 0.0;
-        for (int b = 0; b < nblk; ++b) v += part[(size_t)b * (kAAMax + 1) + s];
-        d[s] = v;
-    }
     for (int s = 0; s < slots; ++s) {
         Q[slot * slots + s] = d[s];
         Q[s * slots + slot] = d[s];

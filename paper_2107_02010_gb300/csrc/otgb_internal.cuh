@@ -135,6 +135,8 @@ struct SoftminLaunch {
     unsigned int *tc_err;    // set when a bounded tensor-core wait gave up (may be null)
     const int4 *fin;         // finalize list (split mode)
     int n_fin;
+    const int *item_fin;     // split mode, optional: fin entry of each item; with fin_count the warp that
+    int *fin_count;          // completes a block's last item sums its partials (no finalize launch)
     float eps;               // temperature
     float s;                 // log2(e) / eps
     double eps_ln2;          // eps * ln 2 (double)

@@ -90,9 +90,16 @@ __global__ void divsum_final_kernel(const double *part, int nblk, double rho, do
 __global__ void transl_partial_kernel(const float *wa, const float *f, int N, const float *wb, const float *g, int M,
                                       double rho, double2 *part) {
     __shared__ double sa[kRB], sb[kRB];
+    // exp in single precision where it cannot overflow or flush (|t| < 80),
+    // in double elsewhere; the sums in double
+    const float inv_rho = (float)(1.0 / rho);
+    auto term = [&](float w, float v) -> double {
+        const float t = -v * inv_rho;
+        return fabsf(t) < 80.f ? (double)(w * expf(t)) : (double)w * exp(-(double)v / rho);
+    };
     double A = 0.0, B = 0.0;
-    for (int i = blockIdx.x * kRB + threadIdx.x; i < N; i += gridDim.x * kRB) A += (double)wa[i] * exp(-(double)f[i] / rho);
-    for (int j = blockIdx.x * kRB + threadIdx.x; j < M; j += gridDim.x * kRB) B += (double)wb[j] * exp(-(double)g[j] / rho);
+    for (int i = blockIdx.x * kRB + threadIdx.x; i < N; i += gridDim.x * kRB) A += term(wa[i], f[i]);
+    for (int j = blockIdx.x * kRB + threadIdx.x; j < M; j += gridDim.x * kRB) B += term(wb[j], g[j]);
     sa[threadIdx.x] = A;
     sb[threadIdx.x] = B;
     __syncthreads();
@@ -107,13 +114,19 @@ __global__ void transl_partial_kernel(const float *wa, const float *f, int N, co
 __global__ void transl_apply_kernel(const double2 *part, int nblk, double rho, float *f, int N, float *g, int M,
                                     double *c_out) {
     __shared__ float cs;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         double A = 0.0, B = 0.0;
-        for (int b = 0; b < nblk; ++b) { A += part[b].x; B += part[b].y; }
+        for (int b = threadIdx.x; b < nblk; b += 32) { A += part[b].x; B += part[b].y; }
+        for (int o = 16; o > 0; o >>= 1) {
+            A += __shfl_xor_sync(0xffffffffu, A, o);
+            B += __shfl_xor_sync(0xffffffffu, B, o);
+        }
         double c = (A > 0.0 && B > 0.0) ? 0.5 * rho * log(A / B) : 0.0;
         if (!isfinite(c)) c = 0.0;
-        cs = (float)c;
-        if (blockIdx.x == 0 && c_out) *c_out = c;
+        if (threadIdx.x == 0) {
+            cs = (float)c;
+            if (blockIdx.x == 0 && c_out) *c_out = c;
+        }
     }
     __syncthreads();
     const float c = cs;
@@ -372,7 +385,7 @@ void divergence_sum(const float *wa, const float *f, const float *aa, int N, con
 
 void translate_duals(const float *wa, float *f, int N, const float *wb, float *g, int M, double rho, double2 *d_part,
                      double *d_c, cudaStream_t st) {
-    const int nblk = 64;
+    const int nblk = 64;  // d_part holds 64 partials
     transl_partial_kernel<<<nblk, kRB, 0, st>>>(wa, f, N, wb, g, M, rho, d_part);
     OTGB_CHECK_LAUNCH();
     transl_apply_kernel<<<128, 256, 0, st>>>(d_part, nblk, rho, f, N, g, M, d_c);

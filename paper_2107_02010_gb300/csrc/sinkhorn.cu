@@ -227,6 +227,7 @@ void Solver::set_work(const std::vector<std::vector<int>> &ncols, bool allow_spl
         CH = std::max(512, (CH + 127) / 128 * 128);
     }
     std::vector<int4> items, fin;
+    std::vector<int> item_fin;
     for (int k = 0; k < (int)ncols.size(); ++k)
         for (int b = 0; b < (int)ncols[k].size(); ++b) {
             const int n = ncols[k][b];
@@ -234,6 +235,7 @@ void Solver::set_work(const std::vector<std::vector<int>> &ncols, bool allow_spl
             if (n <= CH) items.push_back(make_int4(k, b, 0, n));
             else
                 for (int c = 0; c < n; c += CH) items.push_back(make_int4(k, b, c, std::min(n, c + CH)));
+            item_fin.resize(items.size(), (int)fin.size());
             fin.push_back(make_int4(k, b, first, (int)items.size() - first));
         }
     const bool split = items.size() > fin.size();
@@ -245,12 +247,18 @@ void Solver::set_work(const std::vector<std::vector<int>> &ncols, bool allow_spl
     launch.part = nullptr;
     launch.fin = nullptr;
     launch.n_fin = 0;
+    launch.item_fin = nullptr;
+    launch.fin_count = nullptr;
     if (split) {
         int4 *d_fin = ws->get<int4>(nm("fin"), fin.size() + 1);
         OTGB_CUDA_TRY(cudaMemcpyAsync(d_fin, fin.data(), fin.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
         launch.part = ws->get<float>(nm("part"), items.size() * (size_t)kPartRows);
         launch.fin = d_fin;
         launch.n_fin = (int)fin.size();
+        int *d_ifin = ws->get<int>(nm("itemfin"), items.size() + 1);
+        OTGB_CUDA_TRY(cudaMemcpyAsync(d_ifin, item_fin.data(), item_fin.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        launch.item_fin = d_ifin;
+        launch.fin_count = ws->get<int>(nm("fincnt"), fin.size() + 1);
     }
     OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors go out of scope
 }

@@ -377,9 +377,43 @@ __device__ __forceinline__ void softmin3_item(const SoftminLaunch &L, int it, fl
 
     if (lane == 0 && L.pairs) atomicAdd(L.pairs, (unsigned long long)(r1 - r0) * (unsigned long long)ncol);
     if (L.part) {
-        // split block: partial sums, finished by softmin3_finalize_kernel
+        // split block: partial sums, finished by the warp that completes the
+        // block's last item (or by softmin3_finalize_kernel)
 #pragma unroll
         for (int k = 0; k < R; ++k) L.part[(size_t)it * kPartRows + lane + 32 * k] = tot[k];
+        if (L.fin_count) {
+            __threadfence();
+            int fi = 0, done = 0;
+            if (lane == 0) {
+                fi = L.item_fin[it];
+                OTGB_DCLAMP(fi, 0, L.n_fin);
+                done = atomicAdd(L.fin_count + fi, 1) + 1;
+            }
+            fi = __shfl_sync(0xffffffffu, fi, 0);
+            done = __shfl_sync(0xffffffffu, done, 0);
+            const int4 fe = L.fin[fi];
+            if (done == fe.w) {
+                __threadfence();
+#pragma unroll
+                for (int k = 0; k < R; ++k) tot[k] = 0.f;
+                for (int q = 0; q < fe.w; ++q) {
+                    int item_q = fe.z + q;
+                    OTGB_DCLAMP(item_q, 0, L.n_items);
+#pragma unroll
+                    for (int k = 0; k < R; ++k) tot[k] += __ldcg(L.part + (size_t)item_q * kPartRows + lane + 32 * k);
+                }
+                if constexpr (R >= 2) {
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        float lo, hi;
+                        unpack2(Mn[p], lo, hi);
+                        m[2 * p] = -lo;
+                        m[2 * p + 1] = -hi;
+                    }
+                }
+                finish_rows3<R>(L, I, item.x, blk, r0, r1, c, m, tot);
+            }
+        }
     } else {
         if constexpr (R >= 2) {
 #pragma unroll
@@ -737,6 +771,7 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
     require(!(D > 3 && L.part), "softmin_run: split blocks are D <= 3 only", OTGB_EINTERNAL);
     if (D <= 3) {
         if (L.work_counter) OTGB_CUDA_TRY(cudaMemsetAsync(L.work_counter, 0, sizeof(int), st));
+        if (L.part && L.fin_count) OTGB_CUDA_TRY(cudaMemsetAsync(L.fin_count, 0, sizeof(int) * L.n_fin, st));
         switch (rows_per_thread + (two ? 8 : 0)) {
             case 1: launch_softmin3<1, false>(L, st); break;
             case 2: launch_softmin3<2, false>(L, st); break;
@@ -746,7 +781,7 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
             default: launch_softmin3<4, true>(L, st); break;
         }
         OTGB_CHECK_LAUNCH();
-        if (L.part && L.n_fin > 0) {
+        if (L.part && L.n_fin > 0 && !L.fin_count) {
             const int fgrid = (L.n_fin + kW3 - 1) / kW3;
             switch (rows_per_thread) {
                 case 1: softmin3_finalize_kernel<1><<<fgrid, 32 * kW3, 0, st>>>(L); break;
