@@ -79,6 +79,10 @@ __global__ void aa_solve_kernel(const double *part, int nblk, int slots, int m, 
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         d[s] = v;
     }
+    // the Gram ring in shared memory for the serial part below
+    __shared__ double Qs[(kAAMax + 1) * (kAAMax + 1)];
+    for (int e = lane; e < slots * slots; e += 32) Qs[e] = Q[e];
+    __syncwarp();
     if (lane != 0) return;
     const int slot = state[0];
     int cnt = state[1] + 1;
@@ -86,6 +90,8 @@ __global__ void aa_solve_kernel(const double *part, int nblk, int slots, int m, 
     for (int s = 0; s < slots; ++s) {
         Q[slot * slots + s] = d[s];
         Q[s * slots + slot] = d[s];
+        Qs[slot * slots + s] = d[s];
+        Qs[s * slots + slot] = d[s];
     }
     const double rr = d[slot];
     // safeguard: restart when the residual grew well above the best of this history
@@ -108,9 +114,9 @@ __global__ void aa_solve_kernel(const double *part, int nblk, int slots, int m, 
             const int i0 = idx[cnt - 1 - k + i], i1 = idx[cnt - k + i];
             for (int j = 0; j < k; ++j) {
                 const int j0 = idx[cnt - 1 - k + j], j1 = idx[cnt - k + j];
-                A[i][j] = Q[i1 * slots + j1] - Q[i1 * slots + j0] - Q[i0 * slots + j1] + Q[i0 * slots + j0];
+                A[i][j] = Qs[i1 * slots + j1] - Qs[i1 * slots + j0] - Qs[i0 * slots + j1] + Qs[i0 * slots + j0];
             }
-            bvec[i] = Q[i1 * slots + slot] - Q[i0 * slots + slot];
+            bvec[i] = Qs[i1 * slots + slot] - Qs[i0 * slots + slot];
         }
         double tr = 0.0;
         for (int i = 0; i < k; ++i) tr += A[i][i];

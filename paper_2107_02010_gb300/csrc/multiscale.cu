@@ -144,9 +144,11 @@ __device__ __forceinline__ void flat_to_inst(const ListLaunch &L, int f, int &k,
 // Union of the keep bits of a block's row clusters; each thread owns a
 // contiguous range of words so that the column list comes out in increasing
 // order.  WRITE = false: count the kept columns; true: write them.
+constexpr int kListSmem = 4096;
+
 template <bool WRITE>
 __global__ void list_kernel(const __grid_constant__ ListLaunch L) {
-    __shared__ int scan[256];
+    __shared__ int scan[256], sscan2[256];
     int k, b;
     flat_to_inst(L, blockIdx.x, k, b);
     const ListInst &P = L.inst[k];
@@ -173,24 +175,71 @@ __global__ void list_kernel(const __grid_constant__ ListLaunch L) {
         if (threadIdx.x == 0) L.counts[blockIdx.x] = scan[0];
         return;
     }
-    // exclusive scan of the per-thread counts
+    // Kept clusters of this block in order, with the list position where each
+    // one's columns start, go to shared memory; then the CTA writes the list
+    // with consecutive threads on consecutive positions (each position finds
+    // its cluster by binary search).  Blocks that keep more clusters than fit
+    // write per thread.
+    __shared__ int sJ[kListSmem], sP[kListSmem + 1];
+    __shared__ int nq_tot;
+    int nq = 0;
+    for (int w = w0; w < w1; ++w) {
+        unsigned u = 0;
+        for (int I = cl0; I < cl1; ++I) u |= P.bits[(size_t)I * L.nwords + w];
+        nq += __popc(u);
+    }
+    // exclusive scans of the per-thread column and cluster counts
     scan[threadIdx.x] = cnt;
+    sscan2[threadIdx.x] = nq;
     __syncthreads();
     for (int o = 1; o < (int)blockDim.x; o <<= 1) {
         const int v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+        const int v2 = threadIdx.x >= o ? sscan2[threadIdx.x - o] : 0;
         __syncthreads();
         scan[threadIdx.x] += v;
+        sscan2[threadIdx.x] += v2;
         __syncthreads();
     }
-    int pos = L.col_ptr[blockIdx.x] + scan[threadIdx.x] - cnt;
+    const int base = L.col_ptr[blockIdx.x];
+    int pos = scan[threadIdx.x] - cnt;
+    if (threadIdx.x == blockDim.x - 1) nq_tot = sscan2[threadIdx.x];
+    __syncthreads();
+    const int Q = nq_tot, T = scan[blockDim.x - 1];
+    if (Q > kListSmem) {
+        for (int w = w0; w < w1; ++w) {
+            unsigned u = 0;
+            for (int I = cl0; I < cl1; ++I) u |= P.bits[(size_t)I * L.nwords + w];
+            while (u) {
+                const int J = w * 32 + __ffs(u) - 1;
+                u &= u - 1;
+                for (int j = P.off_c[J]; j < P.off_c[J + 1]; ++j) L.list[base + pos++] = j;
+            }
+        }
+        return;
+    }
+    int q = sscan2[threadIdx.x] - nq;
     for (int w = w0; w < w1; ++w) {
         unsigned u = 0;
         for (int I = cl0; I < cl1; ++I) u |= P.bits[(size_t)I * L.nwords + w];
         while (u) {
             const int J = w * 32 + __ffs(u) - 1;
             u &= u - 1;
-            for (int j = P.off_c[J]; j < P.off_c[J + 1]; ++j) L.list[pos++] = j;
+            sJ[q] = J;
+            sP[q] = pos;
+            pos += P.off_c[J + 1] - P.off_c[J];
+            ++q;
         }
+    }
+    if (threadIdx.x == 0) sP[Q] = T;
+    __syncthreads();
+    for (int p = threadIdx.x; p < T; p += blockDim.x) {
+        int lo = 0, hi = Q - 1;  // the last q with sP[q] <= p
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sP[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        L.list[base + p] = P.off_c[sJ[lo]] + (p - sP[lo]);
     }
 }
 
