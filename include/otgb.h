@@ -40,7 +40,11 @@ typedef enum {
     OTGB_EINTERNAL = -7   /* internal consistency check failed */
 } otgb_status;
 
-typedef enum { OTGB_FP32 = 0, OTGB_TC_BF16X3 = 1 } otgb_precision;
+/* OTGB_FP32: float32 accuracy; for D <= 3 the exponent of every pair is one tensor-core dot
+   product of three-piece BF16 operands (about 24 significant bits) with FP32 accumulation,
+   elsewhere CUDA-core float32.  OTGB_TC_BF16X3: the reduced-precision tensor-core cross term
+   for D >= 16 (about 16 bits).  OTGB_FP32_SIMT: float32 on the CUDA cores for every D. */
+typedef enum { OTGB_FP32 = 0, OTGB_TC_BF16X3 = 1, OTGB_FP32_SIMT = 2 } otgb_precision;
 typedef enum { OTGB_CLUSTER_GRID = 0, OTGB_CLUSTER_KMEANS = 1 } otgb_cluster_kind;
 
 /* Opaque handles. */

@@ -54,6 +54,7 @@ struct Solver {
     bool timing = false;
     bool translation = false;
     bool use_tc = false;
+    bool use_tc3 = false;
     std::vector<cudaEvent_t> ev_pool;
     int ev_used = 0;
     double softmin_ms = 0.0;

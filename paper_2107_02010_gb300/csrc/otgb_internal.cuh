@@ -132,6 +132,7 @@ struct SoftminLaunch {
     float *part;             // null: every block is a single item, finished inline
     int exact_max;           // 1: take each row's shift from an exact maximum pass even when old values exist
     int use_tc;              // 1: D >= 16 cross term on the tensor cores (BF16 hi/lo split, FP32 accumulate)
+    int use_tc3;             // 1: D <= 3 exponent on the tensor cores (three-piece BF16, float32 accuracy)
     unsigned int *tc_err;    // set when a bounded tensor-core wait gave up (may be null)
     const int4 *fin;         // finalize list (split mode)
     int n_fin;
@@ -156,6 +157,9 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
 
 // Tensor-core softmin (softmin_tc.cu), D >= 16, old values required, blocks <= 128 rows.
 void softmin_tc_launch(const SoftminLaunch &L, int D, cudaStream_t st);
+// Tensor-core D <= 3 softmin at float32 accuracy (softmin3_tc.cu): old values required,
+// blocks <= 128 rows, split blocks only with item_fin / fin_count.
+void softmin3_tc_launch(const SoftminLaunch &L, cudaStream_t st);
 size_t softmin_tc_smem_bytes();
 
 // Build uniform row blocks of `block_rows` rows for an instance of n rows:

@@ -277,6 +277,7 @@ void Solver::alloc_common() {
     launch.tc_err = ws->get<unsigned>(nm("tcerr"), 1);
     OTGB_CUDA_TRY(cudaMemsetAsync(launch.tc_err, 0, sizeof(unsigned), st));
     launch.use_tc = use_tc ? 1 : 0;
+    launch.use_tc3 = use_tc3 ? 1 : 0;
     OTGB_CUDA_TRY(cudaMemsetAsync(d_fb_total, 0, sizeof(unsigned long long), st));
     OTGB_CUDA_TRY(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
     if (timing && ev_pool.empty()) {
@@ -471,8 +472,9 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         require(P.blur > 0.0 && std::isfinite(P.blur), "sinkhorn_divergence: blur must be > 0");
         require(P.scaling > 0.0 && P.scaling < 1.0, "sinkhorn_divergence: scaling must be in (0, 1)");
         require(P.max_iters >= 1, "sinkhorn_divergence: max_iters must be >= 1");
-        require(P.precision == OTGB_FP32 || (P.precision == OTGB_TC_BF16X3 && D >= 16),
-                "sinkhorn_divergence: the tensor-core form needs D >= 16");
+        require(P.precision == OTGB_FP32 || P.precision == OTGB_FP32_SIMT ||
+                    (P.precision == OTGB_TC_BF16X3 && D >= 16),
+                "sinkhorn_divergence: precision must be FP32, FP32_SIMT, or TC_BF16X3 with D >= 16");
         if (plan_out) *plan_out = nullptr;
 
         Solver s;
@@ -485,6 +487,7 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         s.timing = stats != nullptr;
         s.translation = P.translation != 0;
         s.use_tc = P.precision == OTGB_TC_BF16X3 && D >= 16;
+        s.use_tc3 = P.precision == OTGB_FP32 && D <= 3;
         cudaStream_t st = s.st;
         OTGB_CUDA_TRY(cudaEventRecord(ctx_event(ctx, 0), st));
 

@@ -769,7 +769,10 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
     for (int k = 0; k < L.n_inst; ++k) two = two || (L.inst[k].row_old == nullptr);
     require(!(two && L.part), "softmin_run: split blocks need old values", OTGB_EINTERNAL);
     require(!(D > 3 && L.part), "softmin_run: split blocks are D <= 3 only", OTGB_EINTERNAL);
-    if (D <= 3) {
+    if (D <= 3 && L.use_tc3 && !two && rows_per_thread <= 4 && (!L.part || L.fin_count)) {
+        if (L.part) OTGB_CUDA_TRY(cudaMemsetAsync(L.fin_count, 0, sizeof(int) * L.n_fin, st));
+        softmin3_tc_launch(L, st);
+    } else if (D <= 3) {
         if (L.work_counter) OTGB_CUDA_TRY(cudaMemsetAsync(L.work_counter, 0, sizeof(int), st));
         if (L.part && L.fin_count) OTGB_CUDA_TRY(cudaMemsetAsync(L.fin_count, 0, sizeof(int) * L.n_fin, st));
         switch (rows_per_thread + (two ? 8 : 0)) {

@@ -1,0 +1,357 @@
+// Tensor-core form of the D <= 3 softmin sweep at float32 accuracy.
+//
+// The whole exponent of a pair,
+//   v_ij = s xt_i . yt_j + H_j - m_i,   H_j = s (eps log w_j + pot_j - |yt_j|^2 / 2),
+// is one dot product of length K = 32 between a row vector and a column
+// vector of BF16 values, computed by tcgen05.mma with FP32 accumulation in
+// tensor memory, so that the CUDA cores only evaluate ex2 and the sum.  Every
+// float operand is split into three BF16 pieces (h + m + l, about 24
+// significant bits, i.e. float32 accuracy); per coordinate the six products
+// that matter at that accuracy (h.h, h.m, m.h, h.l, l.h, m.m) take six K
+// slots, so the three coordinates use 18 slots.  H_j - C goes in three slots
+// against 1.0, and the row shift -(m_i - C), rounded to BF16, in one slot
+// against 1.0; C is the largest row shift of the block, so that the folded
+// terms are small for every pair that matters.  The finish adds back exactly
+// the shift the accumulator applied, in double precision.
+//
+// One CTA (4 warps) owns a row block of at most 128 rows (one tensor-memory
+// lane per row); columns come in tiles of kN.  Column staging is software
+// pipelined: the indices of tile t+2 and the point of tile t+1 are loaded
+// while the tensor core multiplies tile t+1 and the CTA sums tile t.  Every
+// wait is bounded.  Split blocks write partial sums; the CTA that completes a
+// block's last item sums them in item order and finishes the rows.
+#include <cfloat>
+#include <cmath>
+
+#include <cuda_bf16.h>
+
+#include "otgb_internal.cuh"
+#include "tcgen05.cuh"
+
+namespace otgb {
+namespace {
+
+constexpr int kM = 128, kN = 128, kK = 32;
+constexpr int kATile = kM * kK * 2;  // 8 KiB
+constexpr int kBTile = kN * kK * 2;
+constexpr uint32_t kTmemCols = 2 * kN;
+
+struct Tc3Smem {
+    unsigned char a[kATile];
+    unsigned char b[2][kBTile];
+    float red[4][8];
+    int bc[2];
+    unsigned long long mbar[2];
+    uint32_t tslot;
+};
+
+// K-major canonical layout of a tile with 32 K-columns: 8-row x 16-byte core
+// matrices, 4 along K (leading byte offset 128), 8-row groups 512 bytes apart
+__device__ __forceinline__ int off32(int r, int k) {
+    return (r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint64_t sdesc32(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ float ex2f(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ uint16_t bfbits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float bfval(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+// v ~ h + m + l in BF16 (about 24 significant bits)
+__device__ __forceinline__ void split3(float v, uint16_t &h, uint16_t &m, uint16_t &l) {
+    h = bfbits(v);
+    const float r = v - bfval(h);
+    m = bfbits(r);
+    l = bfbits(r - bfval(m));
+}
+
+__device__ __forceinline__ uint32_t pk(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+
+constexpr uint16_t kOne = 0x3F80;  // 1.0 in BF16
+
+__global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_constant__ SoftminLaunch L) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    Tc3Smem &S = *reinterpret_cast<Tc3Smem *>(smem_raw);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int it = blockIdx.x;
+    int4 item = L.items[it];
+    OTGB_DCLAMP(item.x, 0, L.n_inst);
+    const SoftminInst &I = L.inst[item.x];
+    const int blk = item.y;
+    int r0 = I.blk_row0[blk], r1 = I.blk_row0[blk + 1];
+    OTGB_DCLAMP(r0, 0, I.n_rows + 1);
+    OTGB_DCLAMP(r1, r0, min(I.n_rows, r0 + kM) + 1);
+    const int nr = r1 - r0;
+    const float eps = L.eps, s = L.s;
+    const float4 *rows4 = reinterpret_cast<const float4 *>(I.rows);
+    const float4 *cols4 = reinterpret_cast<const float4 *>(I.cols);
+
+    // ---- rows: centre of the block's bounding box, shifts, the row operand
+    const bool valid = t < nr;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) p = rows4[r0 + t];
+    {
+        float v[6] = {valid ? p.x : FLT_MAX, valid ? p.y : FLT_MAX, valid ? p.z : FLT_MAX,
+                      valid ? -p.x : FLT_MAX, valid ? -p.y : FLT_MAX, valid ? -p.z : FLT_MAX};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            for (int o = 16; o > 0; o >>= 1) v[q] = fminf(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+            if (lane == 0) S.red[warp][q] = v[q];
+        }
+    }
+    if (t == 0) {
+        tc::mbar_init(&S.mbar[0], 1);
+        tc::mbar_init(&S.mbar[1], 1);
+        tc::mbar_init_fence();
+    }
+    __syncthreads();
+    float c[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float lo = fminf(fminf(S.red[0][d], S.red[1][d]), fminf(S.red[2][d], S.red[3][d]));
+        const float nhi = fminf(fminf(S.red[0][d + 3], S.red[1][d + 3]), fminf(S.red[2][d + 3], S.red[3][d + 3]));
+        c[d] = 0.5f * (lo - nhi);
+    }
+    const float x0 = valid ? p.x - c[0] : 0.f, x1 = valid ? p.y - c[1] : 0.f, x2 = valid ? p.z - c[2] : 0.f;
+    const double hx = 0.5 * ((double)x0 * x0 + (double)x1 * x1 + (double)x2 * x2);
+    float m = -INFINITY;
+    if (valid) m = (float)((double)s * (hx - (double)I.row_old[r0 + t] / (double)I.lam));
+    __syncthreads();  // S.red is reused
+    {
+        float mx = m;
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) S.red[warp][6] = mx;
+    }
+    __syncthreads();
+    float Cb = fmaxf(fmaxf(S.red[0][6], S.red[1][6]), fmaxf(S.red[2][6], S.red[3][6]));
+    if (!(Cb > -INFINITY)) Cb = 0.f;
+    const uint16_t mb = valid ? bfbits(-(m - Cb)) : (uint16_t)0;
+    const double m_eff = (double)Cb - (double)bfval(mb);  // the shift the accumulator applies
+    {
+        uint16_t h[3], md[3], l[3];
+        split3(s * x0, h[0], md[0], l[0]);
+        split3(s * x1, h[1], md[1], l[1]);
+        split3(s * x2, h[2], md[2], l[2]);
+        uint32_t w[16];
+        // slots 6d .. 6d+5: h h m h l m (against the column's h m h l h m)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int b0 = 3 * d;  // three words per coordinate
+            w[b0] = pk(h[d], h[d]);
+            w[b0 + 1] = pk(md[d], h[d]);
+            w[b0 + 2] = pk(l[d], md[d]);
+        }
+        w[9] = pk(kOne, kOne);  // slots 18, 19: against H pieces 1, 2
+        w[10] = pk(kOne, mb);   // slot 20: H piece 3; slot 21: the shift
+#pragma unroll
+        for (int q = 11; q < 16; ++q) w[q] = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4 *>(S.a + off32(t, 8 * q)) =
+                make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    }
+
+    // ---- columns of this item
+    const int *list = I.col_list;
+    int c0 = 0, c1 = I.n_cols;
+    if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
+    int cb = item.z, ce = item.w;
+    OTGB_DCLAMP(cb, 0, c1 - c0 + 1);
+    OTGB_DCLAMP(ce, cb, c1 - c0 + 1);
+    const int ncol = ce - cb;
+    const int ntiles = (ncol + kN - 1) / kN;
+    (void)c1;
+
+    // thread t stages column t of each tile
+    auto load_idx = [&](int tile) -> int {
+        const int pp = tile * kN + t;
+        int jj = -1;
+        if (tile < ntiles && pp < ncol) {
+            jj = list ? list[c0 + cb + pp] : cb + pp;
+            OTGB_DCLAMP(jj, 0, I.n_cols);
+        }
+        return jj;
+    };
+    int jc = -1, jn = -1;
+    float4 rq = make_float4(0.f, 0.f, 0.f, 0.f);
+    float rpot = 0.f;
+    auto load_raw = [&]() {
+        if (jc >= 0) {
+            rq = cols4[jc];
+            rpot = I.col_pot[jc];
+        }
+    };
+    auto convert = [&](int buf) {
+        const bool okc = jc >= 0;
+        const float y0 = okc ? rq.x - c[0] : 0.f, y1 = okc ? rq.y - c[1] : 0.f, y2 = okc ? rq.z - c[2] : 0.f;
+        const float sq = y0 * y0 + y1 * y1 + y2 * y2;
+        const float H = okc ? s * (fmaf(eps, rq.w, rpot) - 0.5f * sq) - Cb : -1e30f;
+        uint16_t h[3], md[3], l[3], hh[3];
+        split3(y0, h[0], md[0], l[0]);
+        split3(y1, h[1], md[1], l[1]);
+        split3(y2, h[2], md[2], l[2]);
+        split3(H, hh[0], hh[1], hh[2]);
+        uint32_t w[16];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int b0 = 3 * d;
+            w[b0] = pk(h[d], md[d]);
+            w[b0 + 1] = pk(h[d], l[d]);
+            w[b0 + 2] = pk(h[d], md[d]);
+        }
+        w[9] = pk(hh[0], hh[1]);
+        w[10] = pk(hh[2], kOne);
+#pragma unroll
+        for (int q = 11; q < 16; ++q) w[q] = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4 *>(S.b[buf] + off32(t, 8 * q)) =
+                make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    };
+
+    if (warp == 0) tc::tmem_alloc(&S.tslot, kTmemCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = S.tslot;
+    const uint32_t idesc = tc::idesc_bf16(kM, kN);
+    auto issue = [&](int buf) {
+        const uint32_t d = tmem + (uint32_t)(buf * kN);
+        const uint32_t a = tc::smem_u32(S.a), b = tc::smem_u32(S.b[buf]);
+#pragma unroll
+        for (int kk = 0; kk < kK / 16; ++kk)
+            tc::mma_bf16(d, sdesc32(a + kk * 256), sdesc32(b + kk * 256), idesc, kk > 0 ? 1u : 0u);
+        tc::commit(&S.mbar[buf]);
+    };
+
+    float tot = 0.f;
+    uint32_t phase[2] = {0u, 0u};
+    bool ok = true;
+    // rows of this warp that exist: the epilogue of an empty warp is skipped
+    const bool warp_rows = warp * 32 < nr;
+    if (ntiles > 0) {
+        jc = load_idx(0);
+        load_raw();
+        convert(0);
+        jc = load_idx(1);
+        load_raw();
+        jn = load_idx(2);
+    }
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (t == 0 && ntiles > 0) issue(0);
+    for (int tt = 0; tt < ntiles; ++tt) {
+        const int buf = tt & 1;
+        if (tt + 1 < ntiles) {
+            convert(buf ^ 1);  // tile tt+1 from registers
+            jc = jn;
+            load_raw();            // tile tt+2
+            jn = load_idx(tt + 3);
+        }
+        tc::fence_proxy_async();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (t == 0 && tt + 1 < ntiles) issue(buf ^ 1);
+        if (!tc::mbar_wait(&S.mbar[buf], phase[buf])) ok = false;
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+        phase[buf] ^= 1u;
+        tc::fence_after();
+        if (ok && warp_rows) {
+#pragma unroll
+            for (int cc = 0; cc < kN; cc += 32) {
+                uint32_t v[32];
+                tc::ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kN + cc), v);
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+                for (int q = 0; q < 32; q += 4) {
+                    a0 += ex2f(__uint_as_float(v[q]));
+                    a1 += ex2f(__uint_as_float(v[q + 1]));
+                    a2 += ex2f(__uint_as_float(v[q + 2]));
+                    a3 += ex2f(__uint_as_float(v[q + 3]));
+                }
+                tot += (a0 + a1) + (a2 + a3);
+            }
+        }
+        tc::fence_before();
+        __syncthreads();  // the buffers of this tile are free again
+    }
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok && t == 0 && L.tc_err) atomicOr(L.tc_err, 1u);
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (!ok) return;  // uniform
+
+    if (t == 0 && L.pairs) atomicAdd(L.pairs, (unsigned long long)nr * (unsigned long long)ncol);
+
+    if (L.part) {
+        // split block: partial sums; the CTA that completes the block's last item finishes it
+        L.part[(size_t)it * kPartRows + t] = tot;
+        __threadfence();
+        __syncthreads();
+        if (t == 0) {
+            int fi = L.item_fin[it];
+            OTGB_DCLAMP(fi, 0, L.n_fin);
+            S.bc[0] = fi;
+            S.bc[1] = atomicAdd(L.fin_count + fi, 1) + 1;
+        }
+        __syncthreads();
+        const int4 fe = L.fin[S.bc[0]];
+        if (S.bc[1] != fe.w) return;  // uniform
+        __threadfence();
+        tot = 0.f;
+        for (int q = 0; q < fe.w; ++q) {
+            int iq = fe.z + q;
+            OTGB_DCLAMP(iq, 0, L.n_items);
+            tot += __ldcg(L.part + (size_t)iq * kPartRows + t);
+        }
+    }
+    float dmax = 0.f;
+    if (valid) {
+        const int r = r0 + t;
+        if (!(tot >= 0x1p-60f && tot <= 0x1p60f)) {
+            const int k = atomicAdd(L.n_fallback, 1);
+            if (k < L.fallback_cap) L.fallback[k] = make_int4(item.x, r, blk, 0);
+        } else {
+            const double L2 = m_eff + log2((double)tot);
+            const double tilde = -(double)I.lam * (L.eps_ln2 * L2 - hx);
+            double nw = tilde;
+            if (I.row_old) {
+                const double old = (double)I.row_old[r];
+                nw = old + (double)I.omega * (tilde - old);
+                dmax = (float)(fabs(nw - old) / (double)L.eps);
+            }
+            I.row_out[r] = (float)nw;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if (lane == 0 && L.delta_max) atomicMax(L.delta_max, __float_as_uint(dmax));
+}
+
+}  // namespace
+
+void softmin3_tc_launch(const SoftminLaunch &L, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(Tc3Smem)));
+        attr = true;
+    }
+    softmin3_tc_kernel<<<L.n_items, 128, sizeof(Tc3Smem), st>>>(L);
+    OTGB_CHECK_LAUNCH();
+}
+
+}  // namespace otgb
