@@ -220,7 +220,12 @@ void Solver::set_work(const std::vector<std::vector<int>> &ncols, bool allow_spl
     double W = 0.0;
     for (auto &v : ncols)
         for (int c : v) W += c;
-    const double target = 3.0 * 5.0 * 4.0 * sms;
+#ifndef OTGB_TC3_ITEMS_PER_SM
+#define OTGB_TC3_ITEMS_PER_SM 10.0
+#endif
+    // D <= 3 warp kernel: about three waves of warps (6 CTAs of 4 warps per SM);
+    // tensor-core form: one CTA per item, fewer and longer items
+    const double target = use_tc3 ? OTGB_TC3_ITEMS_PER_SM * sms : 3.0 * 5.0 * 4.0 * sms;
     int CH = 1 << 30;
     if (allow_split) {
         CH = (int)std::ceil(W / target);

@@ -31,17 +31,41 @@
 namespace otgb {
 namespace {
 
-constexpr int kM = 128, kN = 128, kK = 32;
+// Measured on the track-density workload (softmin rate): 256-column tiles with
+// one accumulator and two warpgroups 5.0e12 pairs/s; 128 columns with two
+// accumulators 4.4-4.6e12; deeper pipelines (4-8 accumulators) were slower,
+// the per-tile CTA barriers dominating.
+#ifndef OTGB_TC3_N
+#define OTGB_TC3_N 256
+#endif
+#ifndef OTGB_TC3_STAGES
+#define OTGB_TC3_STAGES 1
+#endif
+#ifndef OTGB_TC3_MINB
+#define OTGB_TC3_MINB 2
+#endif
+#ifndef OTGB_TC3_THREADS
+#define OTGB_TC3_THREADS 256
+#endif
+// Column tiles of kN columns; kStages accumulators in tensor memory and as
+// many staged column tiles, so that the MMA of a tile is issued kStages - 1
+// tiles before its sums are taken.
+// kThreads = 256: two warpgroups read the same tensor-memory lanes (rows) and
+// each takes half of a tile's columns in the epilogue.
+constexpr int kM = 128, kN = OTGB_TC3_N, kK = 32, kStages = OTGB_TC3_STAGES, kThreads = OTGB_TC3_THREADS;
+constexpr int kHalves = kThreads / 128;
 constexpr int kATile = kM * kK * 2;  // 8 KiB
 constexpr int kBTile = kN * kK * 2;
-constexpr uint32_t kTmemCols = 2 * kN;
+constexpr uint32_t kTmemCols = kStages * kN <= 32 ? 32u : (kStages * kN <= 64 ? 64u : (kStages * kN <= 128 ? 128u
+                                   : (kStages * kN <= 256 ? 256u : 512u)));
 
 struct Tc3Smem {
     unsigned char a[kATile];
-    unsigned char b[2][kBTile];
+    unsigned char b[kStages][kBTile];
     float red[4][8];
+    float tot1[128];
     int bc[2];
-    unsigned long long mbar[2];
+    unsigned long long mbar[kStages];
     uint32_t tslot;
 };
 
@@ -80,10 +104,11 @@ __device__ __forceinline__ uint32_t pk(uint16_t lo, uint16_t hi) { return (uint3
 
 constexpr uint16_t kOne = 0x3F80;  // 1.0 in BF16
 
-__global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_constant__ SoftminLaunch L) {
+__global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(const __grid_constant__ SoftminLaunch L) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Tc3Smem &S = *reinterpret_cast<Tc3Smem *>(smem_raw);
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int t = tid & 127, half = tid >> 7;  // row (tensor-memory lane) and warpgroup
     const int it = blockIdx.x;
     int4 item = L.items[it];
     OTGB_DCLAMP(item.x, 0, L.n_inst);
@@ -98,10 +123,10 @@ __global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_consta
     const float4 *cols4 = reinterpret_cast<const float4 *>(I.cols);
 
     // ---- rows: centre of the block's bounding box, shifts, the row operand
-    const bool valid = t < nr;
+    const bool valid = half == 0 && t < nr;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) p = rows4[r0 + t];
-    {
+    if (half == 0) {
         float v[6] = {valid ? p.x : FLT_MAX, valid ? p.y : FLT_MAX, valid ? p.z : FLT_MAX,
                       valid ? -p.x : FLT_MAX, valid ? -p.y : FLT_MAX, valid ? -p.z : FLT_MAX};
 #pragma unroll
@@ -110,9 +135,8 @@ __global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_consta
             if (lane == 0) S.red[warp][q] = v[q];
         }
     }
-    if (t == 0) {
-        tc::mbar_init(&S.mbar[0], 1);
-        tc::mbar_init(&S.mbar[1], 1);
+    if (tid == 0) {
+        for (int q = 0; q < kStages; ++q) tc::mbar_init(&S.mbar[q], 1);
         tc::mbar_init_fence();
     }
     __syncthreads();
@@ -128,7 +152,7 @@ __global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_consta
     float m = -INFINITY;
     if (valid) m = (float)((double)s * (hx - (double)I.row_old[r0 + t] / (double)I.lam));
     __syncthreads();  // S.red is reused
-    {
+    if (half == 0) {
         float mx = m;
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) S.red[warp][6] = mx;
@@ -138,7 +162,7 @@ __global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_consta
     if (!(Cb > -INFINITY)) Cb = 0.f;
     const uint16_t mb = valid ? bfbits(-(m - Cb)) : (uint16_t)0;
     const double m_eff = (double)Cb - (double)bfval(mb);  // the shift the accumulator applies
-    {
+    if (half == 0) {
         uint16_t h[3], md[3], l[3];
         split3(s * x0, h[0], md[0], l[0]);
         split3(s * x1, h[1], md[1], l[1]);
@@ -173,11 +197,12 @@ __global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_consta
     const int ntiles = (ncol + kN - 1) / kN;
     (void)c1;
 
-    // thread t stages column t of each tile
+    // thread tid < kN stages column tid of each tile
+    const bool stager = tid < kN;
     auto load_idx = [&](int tile) -> int {
-        const int pp = tile * kN + t;
+        const int pp = tile * kN + tid;
         int jj = -1;
-        if (tile < ntiles && pp < ncol) {
+        if (stager && tile < ntiles && pp < ncol) {
             jj = list ? list[c0 + cb + pp] : cb + pp;
             OTGB_DCLAMP(jj, 0, I.n_cols);
         }
@@ -193,6 +218,7 @@ __global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_consta
         }
     };
     auto convert = [&](int buf) {
+        if (!stager) return;
         const bool okc = jc >= 0;
         const float y0 = okc ? rq.x - c[0] : 0.f, y1 = okc ? rq.y - c[1] : 0.f, y2 = okc ? rq.z - c[2] : 0.f;
         const float sq = y0 * y0 + y1 * y1 + y2 * y2;
@@ -216,7 +242,7 @@ __global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_consta
         for (int q = 11; q < 16; ++q) w[q] = 0u;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4 *>(S.b[buf] + off32(t, 8 * q)) =
+            *reinterpret_cast<uint4 *>(S.b[buf] + off32(tid, 8 * q)) =
                 make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
     };
 
@@ -236,45 +262,50 @@ __global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_consta
     };
 
     float tot = 0.f;
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase_bits = 0u;  // bit q: parity of the next completion of accumulator q
     bool ok = true;
     // rows of this warp that exist: the epilogue of an empty warp is skipped
-    const bool warp_rows = warp * 32 < nr;
-    if (ntiles > 0) {
-        jc = load_idx(0);
-        load_raw();
-        convert(0);
-        jc = load_idx(1);
-        load_raw();
-        jn = load_idx(2);
+    const bool warp_rows = (warp & 3) * 32 < nr;
+    // prologue: tiles 0 .. kStages-2 staged, tile kStages-1 in registers
+    for (int q = 0; q < kStages - 1; ++q) {
+        if (q < ntiles) {
+            jc = load_idx(q);
+            load_raw();
+            convert(q);
+        }
     }
+    jc = load_idx(kStages - 1);
+    load_raw();
+    jn = load_idx(kStages);
     tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (t == 0 && ntiles > 0) issue(0);
+    if (tid == 0)
+        for (int q = 0; q < kStages - 1 && q < ntiles; ++q) issue(q);
     for (int tt = 0; tt < ntiles; ++tt) {
-        const int buf = tt & 1;
-        if (tt + 1 < ntiles) {
-            convert(buf ^ 1);  // tile tt+1 from registers
+        const int buf = tt % kStages;
+        const int ahead = tt + kStages - 1;  // the tile whose MMA is issued now
+        if (ahead < ntiles) {
+            convert(ahead % kStages);  // from registers
             jc = jn;
-            load_raw();            // tile tt+2
-            jn = load_idx(tt + 3);
+            load_raw();                // tile ahead + 1
+            jn = load_idx(ahead + 2);
         }
         tc::fence_proxy_async();
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
-        if (t == 0 && tt + 1 < ntiles) issue(buf ^ 1);
-        if (!tc::mbar_wait(&S.mbar[buf], phase[buf])) ok = false;
+        if (tid == 0 && ahead < ntiles) issue(ahead % kStages);
+        if (!tc::mbar_wait(&S.mbar[buf], (phase_bits >> buf) & 1u)) ok = false;
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
-        phase[buf] ^= 1u;
+        phase_bits ^= 1u << buf;
         tc::fence_after();
         if (ok && warp_rows) {
 #pragma unroll
-            for (int cc = 0; cc < kN; cc += 32) {
+            for (int cc = half * (kN / kHalves); cc < (half + 1) * (kN / kHalves); cc += 32) {
                 uint32_t v[32];
-                tc::ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kN + cc), v);
+                tc::ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * kN + cc), v);
                 float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
                 for (int q = 0; q < 32; q += 4) {
@@ -290,19 +321,25 @@ __global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_consta
         __syncthreads();  // the buffers of this tile are free again
     }
     ok = __syncthreads_and(ok) != 0;
-    if (!ok && t == 0 && L.tc_err) atomicOr(L.tc_err, 1u);
+    if (!ok && tid == 0 && L.tc_err) atomicOr(L.tc_err, 1u);
     tc::fence_after();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
     if (!ok) return;  // uniform
+    // the two warpgroups' sums of a row
+    if (kHalves > 1) {
+        if (half == 1) S.tot1[t] = tot;
+        __syncthreads();
+        if (half == 0) tot += S.tot1[t];
+    }
 
-    if (t == 0 && L.pairs) atomicAdd(L.pairs, (unsigned long long)nr * (unsigned long long)ncol);
+    if (tid == 0 && L.pairs) atomicAdd(L.pairs, (unsigned long long)nr * (unsigned long long)ncol);
 
     if (L.part) {
         // split block: partial sums; the CTA that completes the block's last item finishes it
-        L.part[(size_t)it * kPartRows + t] = tot;
+        if (half == 0) L.part[(size_t)it * kPartRows + t] = tot;
         __threadfence();
         __syncthreads();
-        if (t == 0) {
+        if (tid == 0) {
             int fi = L.item_fin[it];
             OTGB_DCLAMP(fi, 0, L.n_fin);
             S.bc[0] = fi;
@@ -313,11 +350,12 @@ __global__ void __launch_bounds__(128, 2) softmin3_tc_kernel(const __grid_consta
         if (S.bc[1] != fe.w) return;  // uniform
         __threadfence();
         tot = 0.f;
-        for (int q = 0; q < fe.w; ++q) {
-            int iq = fe.z + q;
-            OTGB_DCLAMP(iq, 0, L.n_items);
-            tot += __ldcg(L.part + (size_t)iq * kPartRows + t);
-        }
+        if (half == 0)
+            for (int q = 0; q < fe.w; ++q) {
+                int iq = fe.z + q;
+                OTGB_DCLAMP(iq, 0, L.n_items);
+                tot += __ldcg(L.part + (size_t)iq * kPartRows + t);
+            }
     }
     float dmax = 0.f;
     if (valid) {
@@ -350,7 +388,7 @@ void softmin3_tc_launch(const SoftminLaunch &L, cudaStream_t st) {
                                            (int)sizeof(Tc3Smem)));
         attr = true;
     }
-    softmin3_tc_kernel<<<L.n_items, 128, sizeof(Tc3Smem), st>>>(L);
+    softmin3_tc_kernel<<<L.n_items, kThreads, sizeof(Tc3Smem), st>>>(L);
     OTGB_CHECK_LAUNCH();
 }
 
