@@ -31,12 +31,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# Measured per-SM, per-clock rates on GB300 (sm_103a): ex2.approx 32/clk,
-# FP32 FMA 128 lanes/clk (f32x2 packing halves issue, not FP32 work).  A pair of
-# a stable log-sum-exp in the dot-product form costs D FMAs, one add (the row's
-# reference), one add (accumulate) and one ex2.
+# Measured per-SM, per-clock rates on GB300 (sm_103a): ex2.approx 32/clk (the
+# MUFU unit), FP32 FMA 128 lanes/clk (f32x2 packing halves issue, not FP32 work).
+# A pair of a stable log-sum-exp in the dot-product form costs D FMAs, one add
+# (the row's reference), one add (accumulate) and one ex2 on the CUDA cores; in
+# the tensor-core forms the exponent comes from the tensor core and the CUDA
+# cores keep one ex2 and one add per pair, so the MUFU unit bounds them.
 SFU_EX2_PER_CLK_SM = 32
 FP32_LANES_PER_CLK_SM = 128
+# D <= 3, default precision: tensor-core dot product of K = 32 BF16 slots per pair
+TC3_TENSOR_FLOP_PER_PAIR = 2 * 32
 
 
 def workload(args):
@@ -220,7 +224,15 @@ def run_fibers(args):
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     clk = peaks.get("sm_max_mhz", 2070.0)
     D = x.shape[1]
-    peak = peak_pairs_per_s(D, clk, n_sm)
+    if args.precision == "tc":
+        # three K = 64 BF16 MMAs per pair (hi.hi, hi.lo, lo.hi); the MUFU bound is higher
+        peak = min(peaks.get("bf16_tflops", 1929.8) * 1e12 / (3 * 2 * 64), SFU_EX2_PER_CLK_SM * n_sm * clk * 1e6)
+        basis = "tensor: bf16 of measured / 384 flop per pair (MUFU %d SMs x 32/clk is higher)" % n_sm
+        bound = "tensor"
+    else:
+        peak = peak_pairs_per_s(D, clk, n_sm)
+        basis = "FP32 form: %d SMs x min(32, 128/(D+2)) pairs/clk x %.0f MHz" % (n_sm, clk)
+        bound = "alu"
     achieved = pairs / (smin / 1e3) if smin > 0 else None
     line = {"metric": "softmin pairs/s", "workload": "fibers", "value": pairs / (sum(ms) / 1e3), "unit": "pairs/s",
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
@@ -230,9 +242,8 @@ def run_fibers(args):
                                    (args.n, max(20, args.n // 1000), args.precision)},
             "time_to_solve_ms": statistics.mean(ms), "iters_per_solve": out["stats"]["iters_total"],
             "S": out["S"], "last_stats": out["stats"],
-            "roofline": {"bound": "alu", "achieved": achieved / 1e9 if achieved else None, "peak": peak / 1e9,
-                         "unit": "Gpairs/s", "frac": achieved / peak if achieved else None,
-                         "peak_basis": "FP32 form: %d SMs x min(32, 128/(D+2)) pairs/clk x %.0f MHz" % (n_sm, clk)},
+            "roofline": {"bound": bound, "achieved": achieved / 1e9 if achieved else None, "peak": peak / 1e9,
+                         "unit": "Gpairs/s", "frac": achieved / peak if achieved else None, "peak_basis": basis},
             "gpu_launches": int(otgb.kernel_launches() - l0), "clocks": clocks}
     print(json.dumps(line))
     return 0
@@ -378,7 +389,11 @@ def main():
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     clk = peaks.get("sm_max_mhz", 2070.0)
-    peak = peak_pairs_per_s(3, clk, n_sm)
+    # the default D <= 3 kernel (softmin3_tc_kernel): min(MUFU ex2, tensor pipe)
+    peak_mufu = SFU_EX2_PER_CLK_SM * n_sm * clk * 1e6
+    peak_tensor = peaks.get("bf16_tflops", 1929.8) * 1e12 / TC3_TENSOR_FLOP_PER_PAIR
+    peak = min(peak_mufu, peak_tensor)
+    peak_fp32_form = peak_pairs_per_s(3, clk, n_sm)
     achieved = pairs / max(world, 1) / (smin_ms / 1e3) if smin_ms > 0 else None
 
     if rank != 0:
@@ -401,11 +416,15 @@ def main():
         "last_stats": out["stats"],
         "softmin_ms_per_solve": smin_ms / args.steps,
         "pairs_per_solve": pairs_per,
-        "roofline": {"bound": "alu", "kernel": "softmin3_kernel (+ fallback, per softmin launch)",
+        "roofline": {"bound": "alu", "kernel": "softmin3_tc_kernel (+ fallback), per softmin launch",
                      "achieved": achieved / 1e9 if achieved else None, "peak": peak / 1e9, "unit": "Gpairs/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "peak_basis": "%d SMs x min(32 ex2, 128/(D+2) FP32) pairs/clk x %.0f MHz (measured per-clock "
-                                   "rates; clock = sm_max_mhz of MEASURED_PEAKS.json)" % (n_sm, clk)},
+                     "peak_basis": "MUFU ex2: %d SMs x 32 ex2/clk x %.0f MHz (measured per-clock rate; clock = "
+                                   "sm_max_mhz of MEASURED_PEAKS.json), below the tensor bound %.3g pairs/s "
+                                   "(bf16, of measured, %d flop per pair)" % (n_sm, clk, peak_tensor,
+                                                                            TC3_TENSOR_FLOP_PER_PAIR),
+                     "fp32_form_peak": peak_fp32_form / 1e9,
+                     "frac_of_fp32_form_peak": (achieved / peak_fp32_form) if achieved else None},
         "e2e": {"value": e2e_val, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clocks,

@@ -33,8 +33,11 @@ namespace {
 
 // Measured on the track-density workload (softmin rate): 256-column tiles with
 // one accumulator and two warpgroups 5.0e12 pairs/s; 128 columns with two
-// accumulators 4.4-4.6e12; deeper pipelines (4-8 accumulators) were slower,
-// the per-tile CTA barriers dominating.
+// accumulators 4.4-4.6e12; deeper pipelines (4-8 accumulators) were slower;
+// a warp-specialised variant (staging, MMA and sum warps handing tiles over
+// through mbarriers, no CTA barrier per tile) reached 4.6e12; overlapping the
+// tensor-memory loads with the sums changed nothing.  The MUFU ex2 unit (32 per
+// clock per SM) is half busy at 5.0e12.
 #ifndef OTGB_TC3_N
 #define OTGB_TC3_N 256
 #endif
@@ -302,10 +305,11 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
         phase_bits ^= 1u << buf;
         tc::fence_after();
         if (ok && warp_rows) {
-#pragma unroll
-            for (int cc = half * (kN / kHalves); cc < (half + 1) * (kN / kHalves); cc += 32) {
-                uint32_t v[32];
-                tc::ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * kN + cc), v);
+            // the load of chunk k+1 flies while chunk k is summed
+            constexpr int kChunks = kN / kHalves / 32;
+            const uint32_t base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * kN + half * (kN / kHalves));
+            uint32_t va[32], vb[32];
+            auto sum32 = [&](const uint32_t (&v)[32]) {
                 float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
                 for (int q = 0; q < 32; q += 4) {
@@ -315,6 +319,19 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
                     a3 += ex2f(__uint_as_float(v[q + 3]));
                 }
                 tot += (a0 + a1) + (a2 + a3);
+            };
+            tc::ld32_async(base, va);
+            tc::ld_wait(va);
+#pragma unroll
+            for (int k = 0; k < kChunks; k += 2) {
+                if (k + 1 < kChunks) tc::ld32_async(base + 32 * (k + 1), vb);
+                sum32(va);
+                if (k + 1 < kChunks) {
+                    tc::ld_wait(vb);
+                    if (k + 2 < kChunks) tc::ld32_async(base + 32 * (k + 2), va);
+                    sum32(vb);
+                    if (k + 2 < kChunks) tc::ld_wait(va);
+                }
             }
         }
         tc::fence_before();
@@ -378,6 +395,7 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
     for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     if (lane == 0 && L.delta_max) atomicMax(L.delta_max, __float_as_uint(dmax));
 }
+
 
 }  // namespace
 
