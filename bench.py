@@ -41,6 +41,10 @@ SFU_EX2_PER_CLK_SM = 32
 FP32_LANES_PER_CLK_SM = 128
 # D <= 3, default precision: tensor-core dot product of K = 32 BF16 slots per pair
 TC3_TENSOR_FLOP_PER_PAIR = 2 * 32
+# DRAM bytes (read + write) of one fine-step launch of softmin3_tc_kernel on this
+# workload, from one ncu capture (profiles/softmin3_tc_trackdensity_100k_multiscale.md);
+# to be re-measured whenever that kernel changes
+SOFTMIN3_TC_DRAM_BYTES = 172.6e6
 
 
 def workload(args):
@@ -418,7 +422,8 @@ def main():
         "pairs_per_solve": pairs_per,
         "roofline": {"bound": "alu", "kernel": "softmin3_tc_kernel (+ fallback), per softmin launch",
                      "achieved": achieved / 1e9 if achieved else None, "peak": peak / 1e9, "unit": "Gpairs/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": SOFTMIN3_TC_DRAM_BYTES,
+                     "traffic_unit": "bytes per fine-step launch (ncu dram__bytes_read + write)",
                      "peak_basis": "MUFU ex2: %d SMs x 32 ex2/clk x %.0f MHz (measured per-clock rate; clock = "
                                    "sm_max_mhz of MEASURED_PEAKS.json), below the tensor bound %.3g pairs/s "
                                    "(bf16, of measured, %d flop per pair)" % (n_sm, clk, peak_tensor,

@@ -130,13 +130,14 @@ def test_softmin_far_rows_take_the_safe_path(ctx):
 
 
 # -------------------------------------------------------- dense solve ---
-def _run_pair(ctx, x, a, y, b, blur, reach, q, extra):
+def _run_pair(ctx, x, a, y, b, blur, reach, q, extra, precision=0):
     from paper_2107_02010_gb300 import otgb
 
     d = oracle.diameter(x, y)
     n_sched = len(oracle.schedule(d, blur, q))
     # the paper's loop step for step (no translation step), as the oracle runs it
-    p = otgb.default_params(blur=blur, reach=reach, scaling=q, diameter=d, fixed_iters=extra, translation=0)
+    p = otgb.default_params(blur=blur, reach=reach, scaling=q, diameter=d, fixed_iters=extra, translation=0,
+                            precision=precision)
     out = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b), p, want_self=True)
     ref = oracle.sinkhorn(x, a, y, b, blur=blur, reach=reach, scaling=q, diameter=d, tol=0.0,
                           max_iters=n_sched + extra)
@@ -144,11 +145,17 @@ def _run_pair(ctx, x, a, y, b, blur, reach, q, extra):
     return out, ref
 
 
+# precision 0: the D <= 3 exponent on the tensor cores (three-piece BF16, float32
+# accuracy); 2: the CUDA-core float32 kernel -- both must meet the float32 bar
+ENGINES = [0, 2]
+
+
+@pytest.mark.parametrize("precision", ENGINES)
 @pytest.mark.parametrize("reach", [0.0, 0.3])
-def test_dense_solve_same_steps_as_oracle_3d(ctx, reach):
+def test_dense_solve_same_steps_as_oracle_3d(ctx, reach, precision):
     x, a, y, b = synth.rotated_cloud(700, 530, seed=3)
     blur = 0.05
-    out, ref = _run_pair(ctx, x, a, y, b, blur, reach, 0.5, 12)
+    out, ref = _run_pair(ctx, x, a, y, b, blur, reach, 0.5, 12, precision)
     eps = blur ** 2
     check_pots(out, ref, a, b, eps, reach)
     assert abs(out["S"] - ref["S"]) <= TOL * abs(ref["S"]) + 1e-9 * eps, (out["S"], ref["S"])
@@ -188,14 +195,15 @@ def test_single_dirac_closed_form_on_gpu(ctx):
     assert out["S"] == pytest.approx(S_ref, rel=1e-5)
 
 
-def test_converged_solve_matches_converged_oracle(ctx):
+@pytest.mark.parametrize("precision", ENGINES)
+def test_converged_solve_matches_converged_oracle(ctx, precision):
     from paper_2107_02010_gb300 import otgb
 
     x, a, y, b = synth.rotated_cloud(400, 300, seed=9)
     blur, reach = 0.15, 0.5
     ref = oracle.sinkhorn(x, a, y, b, blur=blur, reach=reach, scaling=0.5, tol=1e-12, max_iters=20000)
     assert ref["converged"]
-    p = otgb.default_params(blur=blur, reach=reach, scaling=0.5, tol=1e-7)
+    p = otgb.default_params(blur=blur, reach=reach, scaling=0.5, tol=1e-7, precision=precision)
     out = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b), p, want_self=True)
     eps = blur ** 2
     assert abs(out["S"] - ref["S"]) <= TOL * abs(ref["S"]), (out["S"], ref["S"])

@@ -34,14 +34,20 @@ def rel(got, want, eps):
     return float(np.max(np.abs(got - want)) / (np.max(np.abs(want)) + eps))
 
 
-def test_multiscale_grid_matches_converged_oracle(ctx):
+# precision 0 (tensor-core exponent, float32 accuracy) and 2 (CUDA-core float32)
+ENGINES = [0, 2]
+
+
+@pytest.mark.parametrize("precision", ENGINES)
+def test_multiscale_grid_matches_converged_oracle(ctx, precision):
     from paper_2107_02010_gb300 import otgb
 
     x, a, y, b = synth.density_maps(grid=24, n_tubes=6, n_keep=1500, seeds=(21, 22))
     blur, reach = 1.5, 4.0
     ref = oracle.sinkhorn(x, a, y, b, blur=blur, reach=reach, scaling=0.5, tol=1e-12, max_iters=5000)
     assert ref["converged"]
-    p = otgb.default_params(blur=blur, reach=reach, scaling=0.5, multiscale=1, cluster=0, cell=4.0, tol=1e-8)
+    p = otgb.default_params(blur=blur, reach=reach, scaling=0.5, multiscale=1, cluster=0, cell=4.0, tol=1e-8,
+                            precision=precision)
     out = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b), p, want_self=True)
     st = out["stats"]
     print("stats", st)
@@ -52,15 +58,16 @@ def test_multiscale_grid_matches_converged_oracle(ctx):
         assert rel(out[k], ref[key], eps) < TOL, (k, rel(out[k], ref[key], eps))
 
 
+@pytest.mark.parametrize("precision", ENGINES)
 @pytest.mark.parametrize("n_keep", [20_000])
-def test_multiscale_grid_matches_dense_gpu(ctx, n_keep):
+def test_multiscale_grid_matches_dense_gpu(ctx, n_keep, precision):
     # larger problem: the dense GPU solve (itself parity-checked against the
     # oracle) is the reference; both run to a tight stopping rule
     from paper_2107_02010_gb300 import otgb
 
     x, a, y, b = synth.density_maps(grid=40, n_tubes=15, n_keep=n_keep, seeds=(31, 32))
     blur, reach = 1.0, 10.0
-    common = dict(blur=blur, reach=reach, scaling=0.5, tol=1e-8, max_iters=20000)
+    common = dict(blur=blur, reach=reach, scaling=0.5, tol=1e-8, max_iters=20000, precision=precision)
     dense = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b), otgb.default_params(**common), want_self=True)
     ms = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b),
                                   otgb.default_params(multiscale=1, cluster=0, cell=4.0, **common), want_self=True)
