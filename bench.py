@@ -364,12 +364,9 @@ def main():
 
     ms_per_step = statistics.mean(step_ms)
     t_total = sum(step_ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_total, pairs], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        t_total, pairs = float(mx[0]), float(tt[1])
+    from paper_2107_02010_gb300 import replicas
+
+    t_total, pairs = replicas.aggregate(t_total, pairs, dev)
     value = pairs / t_total
 
     # end to end through the public API with host buffers: pinned host inputs
