@@ -122,17 +122,20 @@ __global__ void aa_solve_kernel(const double *part, int nblk, int slots, int m, 
         for (int i = 0; i < k; ++i) tr += A[i][i];
         const double lam = reg * (tr > 0.0 ? tr / k : 1.0) + 1e-300;
         for (int i = 0; i < k; ++i) A[i][i] += lam;
-        // Cholesky A = L L^T in place (lower triangle)
+        // Cholesky A = L L^T in place (lower triangle); one division per column
+        // (double division and square root are slow on this part)
         bool ok = true;
+        double inv[kAAMax];
         for (int j = 0; j < k && ok; ++j) {
             double s = A[j][j];
             for (int q = 0; q < j; ++q) s -= A[j][q] * A[j][q];
             if (!(s > 0.0)) { ok = false; break; }
             A[j][j] = sqrt(s);
+            inv[j] = 1.0 / A[j][j];
             for (int i = j + 1; i < k; ++i) {
                 double t = A[i][j];
                 for (int q = 0; q < j; ++q) t -= A[i][q] * A[j][q];
-                A[i][j] = t / A[j][j];
+                A[i][j] = t * inv[j];
             }
         }
         double th[kAAMax];
@@ -140,12 +143,12 @@ __global__ void aa_solve_kernel(const double *part, int nblk, int slots, int m, 
             for (int i = 0; i < k; ++i) {
                 double t = bvec[i];
                 for (int q = 0; q < i; ++q) t -= A[i][q] * th[q];
-                th[i] = t / A[i][i];
+                th[i] = t * inv[i];
             }
             for (int i = k - 1; i >= 0; --i) {
                 double t = th[i];
                 for (int q = i + 1; q < k; ++q) t -= A[q][i] * th[q];
-                th[i] = t / A[i][i];
+                th[i] = t * inv[i];
             }
             for (int i = 0; i < k; ++i) ok = ok && isfinite(th[i]);
         }
