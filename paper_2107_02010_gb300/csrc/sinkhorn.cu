@@ -244,6 +244,11 @@ void Solver::set_work(const std::vector<std::vector<int>> &ncols, bool allow_spl
             fin.push_back(make_int4(k, b, first, (int)items.size() - first));
         }
     const bool split = items.size() > fin.size();
+    // Without split blocks the items go longest first (the hardware hands out
+    // CTAs in index order), so that the last wave holds the short items.
+    if (!split)
+        std::stable_sort(items.begin(), items.end(),
+                         [](const int4 &p, const int4 &q) { return p.w - p.z > q.w - q.z; });
     work_ncols = ncols;
     int4 *d_items = ws->get<int4>(nm("items"), items.size() + 1);
     OTGB_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));

@@ -483,27 +483,68 @@ __global__ void __launch_bounds__(32 * kW3) softmin3_finalize_kernel(const __gri
 }
 
 // ------------------------------------------------------------ 3 < D <= 64 --
-// Register-tiled: 256 threads, a block of 128 rows times tiles of 64 columns;
-// each thread computes 8 rows x 4 columns.  Rows are staged once, k-major, as
-// X = s (x - c); column tiles are staged k-major as yt = y - c together with
-// H_j.  The accumulators start at H_j - m_i, so each pair costs D FMAs + one
-// add + ex2 + add.  TWO = true: an exact-maximum first pass over the columns.
+// Register-tiled, packed along the coordinates: 256 threads, a block of 128
+// rows times tiles of 64 columns; each thread computes 8 rows x 4 columns.
+// Rows are staged once as X = s (x - c) and columns per tile as yt = y - c,
+// both as PAIRS of consecutive coordinates (k-pair major), so that one packed
+// f32x2 FMA advances one (row, column) term by two coordinates: the two
+// halves of the accumulator hold the even and the odd partial dot products
+// and are added once at the end.  The k-pair after the last coordinate pair
+// carries the rest of the exponent: (1, -m_i) in the row operand against
+// (H_j, 1) in the column operand, so the accumulator ends at
+// H_j - m_i + X_i . yt_j and the epilogue is one add, ex2 and the sum.
+// Per pair that is D/2 + 1 packed FMAs (D + 2 FP32 operations) for half the
+// instructions of the scalar form.
+//
+// Column tiles flow through a two-stage pipeline without register staging:
+// cp.async copies the raw coordinates (and log w_j, pot_j) of tile t+2 into
+// shared memory while the CTA multiplies tile t; after the products each
+// thread centres and repacks the part of tile t+1 that it copied itself (so
+// the copy needs no barrier), then one barrier per tile.  The column operand
+// is stored with its 16-byte chunks XOR-swizzled by the k-pair, so both the
+// repacking stores and the operand loads are free of bank conflicts.
+// TWO = true: an exact-maximum first pass gives each row's shift.
 constexpr int kNTg = 256;
 constexpr int kBM = 128;
 constexpr int kBN = 64;
+constexpr int kKP = 33;       // 32 coordinate pairs + the folded pair
+constexpr int kXS = kBM + 2;  // float2 stride of a k-pair of X (spreads the staging stores over banks)
 
 struct GenSmem {
-    float xs[64][kBM];      // X, k-major
-    float ys[64][kBN];      // yt, k-major
-    float hs[kBN];          // H
+    float2 xs[kKP][kXS];     // X pairs; pair KPD = (1, -m_i)
+    float2 ys[2][kKP][kBN];  // yt pairs, chunk-swizzled; pair KPD = (H_j, 1)
+    float raw[2][kBN][64];   // raw column coordinates, as copied
+    float rlw[2][kBN];
+    float rpot[2][kBN];
     float cen[64];
-    float hx[kBM];          // |xt|^2 / 2
-    float mrow[kBM];        // per-row shift m_i
+    float hx[kBM];           // |xt|^2 / 2
     float red[kNTg / 32];
 };
 
-template <bool TWO>
-__global__ void __launch_bounds__(kNTg) softmin_gen_kernel(const __grid_constant__ SoftminLaunch L, int D, int D4) {
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// physical 16-byte chunk (two columns) of logical chunk c in k-pair kp
+__device__ __forceinline__ int gen_chunk(int c, int kp) { return c ^ ((kp >> 2) & 7); }
+
+template <bool TWO, int KPT>
+__global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_constant__ SoftminLaunch L, int D, int D4) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GenSmem &S = *reinterpret_cast<GenSmem *>(smem_raw);
     int4 item = L.items[blockIdx.x];
@@ -516,39 +557,40 @@ __global__ void __launch_bounds__(kNTg) softmin_gen_kernel(const __grid_constant
     const int nr = r1 - r0;
     const int t = threadIdx.x;
     const float eps = L.eps, s = L.s;
+    OTGB_DCLAMP(D4, 4, 65);
+    const int KPD = KPT > 0 ? KPT : (D4 >> 1);  // coordinate pairs; pair KPD is the folded one
 
-    // stage raw rows, k-major (zero beyond nr)
+    // ---- rows: raw pairs, centre (mean), X = s (x - c), |xt|^2 / 2, fold pair
+    float *xsf = reinterpret_cast<float *>(&S.xs[0][0]);
     for (int e = t; e < kBM * D4; e += kNTg) {
         const int r = e / D4, k = e - r * D4;
-        S.xs[k][r] = (r < nr) ? I.rows[(size_t)(r0 + r) * D4 + k] : 0.f;
+        xsf[(k >> 1) * (2 * kXS) + 2 * r + (k & 1)] = (r < nr) ? I.rows[(size_t)(r0 + r) * D4 + k] : 0.f;
     }
     __syncthreads();
-    // centre: per-coordinate mean of the block rows
-    for (int k = t; k < D4; k += kNTg) {
+    if (t < 64) {
         float acc = 0.f;
-        for (int r = 0; r < nr; ++r) acc += S.xs[k][r];
-        S.cen[k] = nr > 0 ? acc / (float)nr : 0.f;
-    }
-    __syncthreads();
-    for (int e = t; e < kBM * D4; e += kNTg) {
-        const int k = e / kBM, r = e - k * kBM;
-        S.xs[k][r] = (r < nr) ? S.xs[k][r] - S.cen[k] : 0.f;
+        if (t < D4)
+            for (int r = 0; r < nr; ++r) acc += xsf[(t >> 1) * (2 * kXS) + 2 * r + (t & 1)];
+        S.cen[t] = (t < D4 && nr > 0) ? acc / (float)nr : 0.f;
     }
     __syncthreads();
     if (t < kBM) {
-        float acc = 0.f;
-        for (int k = 0; k < D4; ++k) acc = fmaf(S.xs[k][t], S.xs[k][t], acc);
-        S.hx[t] = 0.5f * acc;
-        S.mrow[t] = 0.f;
-        if (!TWO && t < nr)
-            S.mrow[t] = (float)((double)s * ((double)(0.5f * acc) - (double)I.row_old[r0 + t] / (double)I.lam));
-    }
-    __syncthreads();
-    for (int e = t; e < kBM * D4; e += kNTg) {
-        const int k = e / kBM, r = e - k * kBM;
-        S.xs[k][r] *= s;
+        float sq = 0.f;
+        for (int kp = 0; kp < KPD; ++kp) {
+            float2 v = S.xs[kp][t];
+            v.x = (t < nr) ? v.x - S.cen[2 * kp] : 0.f;
+            v.y = (t < nr) ? v.y - S.cen[2 * kp + 1] : 0.f;
+            sq = fmaf(v.x, v.x, fmaf(v.y, v.y, sq));
+            S.xs[kp][t] = make_float2(s * v.x, s * v.y);
+        }
+        const float h = 0.5f * sq;
+        S.hx[t] = h;
+        float m = 0.f;
+        if (!TWO && t < nr) m = (float)((double)s * ((double)h - (double)I.row_old[r0 + t] / (double)I.lam));
+        S.xs[KPD][t] = make_float2(1.f, -m);
     }
 
+    // ---- columns of this item
     const int *list = I.col_list;
     int c0 = 0, c1 = I.n_cols;
     if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
@@ -557,117 +599,181 @@ __global__ void __launch_bounds__(kNTg) softmin_gen_kernel(const __grid_constant
     OTGB_DCLAMP(ce, cb, c1 - c0 + 1);
     c0 += cb;  // this item sees positions [cb, ce) of the block's columns (never split for D > 3)
     const int ncol = ce - cb;
-    const int tr = t >> 4, tc = t & 15;
     const int ntiles = (ncol + kBN - 1) / kBN;
-    const int D44 = D4 >> 2;
 
-    auto stage = [&](int p0) {
-        __syncthreads();
-        for (int e = t; e < kBN * D44; e += kNTg) {
-            const int col = e % kBN, qq = e / kBN;
-            const int p = p0 + col;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (p < ncol) {
-                int j = list ? list[c0 + p] : p;
-                OTGB_DCLAMP(j, 0, I.n_cols);
-                v = *reinterpret_cast<const float4 *>(I.cols + (size_t)j * D4 + 4 * qq);
-                v.x -= S.cen[4 * qq]; v.y -= S.cen[4 * qq + 1]; v.z -= S.cen[4 * qq + 2]; v.w -= S.cen[4 * qq + 3];
+    // copy/repack roles: chunk ch (coordinates 8 ch .. 8 ch + 7) of columns colb and colb + 32
+    const int ch = t & 7, colb = t >> 3;
+    // product roles: rows 8 tr .. 8 tr + 7, logical chunks tc and tc + 16 (columns 2 tc, 2 tc + 1, +32)
+    const int tr = t >> 4, tc = t & 15;
+
+    auto load_idx = [&](int tile, int (&j)[2]) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int p = tile * kBN + colb + 32 * q;
+            int jj = -1;
+            if (tile < ntiles && p < ncol) {
+                jj = list ? list[c0 + p] : p;
+                OTGB_DCLAMP(jj, 0, I.n_cols);
             }
-            S.ys[4 * qq][col] = v.x; S.ys[4 * qq + 1][col] = v.y; S.ys[4 * qq + 2][col] = v.z; S.ys[4 * qq + 3][col] = v.w;
+            j[q] = jj;
         }
-        __syncthreads();
-        if (t < kBN) {
-            const int p = p0 + t;
-            float acc = 0.f;
-            for (int k = 0; k < D4; ++k) acc = fmaf(S.ys[k][t], S.ys[k][t], acc);
-            float H = -INFINITY;
-            if (p < ncol) {
-                int j = list ? list[c0 + p] : p;
-                OTGB_DCLAMP(j, 0, I.n_cols);
-                const float stuff = fmaf(eps, I.col_logw[j], I.col_pot[j]);
-                H = s * (stuff - 0.5f * acc);
-            }
-            S.hs[t] = H;
-        }
-        __syncthreads();
     };
-    auto dots = [&](float (&acc)[8][4]) {
-#pragma unroll 4
-        for (int k = 0; k < D4; ++k) {
-            const float4 xa = *reinterpret_cast<const float4 *>(&S.xs[k][tr * 8]);
-            const float4 xb = *reinterpret_cast<const float4 *>(&S.xs[k][tr * 8 + 4]);
-            const float4 yv = *reinterpret_cast<const float4 *>(&S.ys[k][tc * 4]);
-            const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-            const float yy[4] = {yv.x, yv.y, yv.z, yv.w};
+    auto issue = [&](int buf, const int (&j)[2]) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(xv[i], yy[jj], acc[i][jj]);
+        for (int q = 0; q < 2; ++q) {
+            const int col = colb + 32 * q;
+            const bool ok = j[q] >= 0;
+            // a copy of size 0 fills zeros and reads nothing; its source is then the valid base
+            const bool k0 = ok && 8 * ch + 4 <= D4, k1 = ok && 8 * ch + 8 <= D4;
+            const float *src = I.cols + (ok ? (size_t)j[q] * D4 + 8 * ch : 0);
+            cp_async16(&S.raw[buf][col][8 * ch], k0 ? src : I.cols, k0 ? 16 : 0);
+            cp_async16(&S.raw[buf][col][8 * ch + 4], k1 ? src + 4 : I.cols, k1 ? 16 : 0);
+            if (ch == 0) {
+                cp_async4(&S.rlw[buf][col], ok ? I.col_logw + j[q] : I.col_logw, ok ? 4 : 0);
+                cp_async4(&S.rpot[buf][col], ok ? I.col_pot + j[q] : I.col_pot, ok ? 4 : 0);
+            }
         }
+    };
+    // centre and repack the part of tile `tile` this thread copied into raw[buf]
+    auto repack = [&](int buf, int tile) {
+        const float4 ca = *reinterpret_cast<const float4 *>(&S.cen[8 * ch]);
+        const float4 cc = *reinterpret_cast<const float4 *>(&S.cen[8 * ch + 4]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int col = colb + 32 * q;
+            const bool ok = tile * kBN + col < ncol;
+            const float4 a = *reinterpret_cast<const float4 *>(&S.raw[buf][col][8 * ch]);
+            const float4 b = *reinterpret_cast<const float4 *>(&S.raw[buf][col][8 * ch + 4]);
+            float v[8] = {a.x - ca.x, a.y - ca.y, a.z - ca.z, a.w - ca.w, b.x - cc.x, b.y - cc.y, b.z - cc.z, b.w - cc.w};
+            float sq = 0.f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                v[e] = ok ? v[e] : 0.f;
+                sq = fmaf(v[e], v[e], sq);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int kp = 4 * ch + e;
+                if (kp < KPD) S.ys[buf][kp][2 * gen_chunk(col >> 1, kp) + (col & 1)] = make_float2(v[2 * e], v[2 * e + 1]);
+            }
+            sq += __shfl_xor_sync(0xffffffffu, sq, 1);
+            sq += __shfl_xor_sync(0xffffffffu, sq, 2);
+            sq += __shfl_xor_sync(0xffffffffu, sq, 4);
+            if (ch == 0) {
+                const float H = ok ? s * (fmaf(eps, S.rlw[buf][col], S.rpot[buf][col]) - 0.5f * sq) : -INFINITY;
+                S.ys[buf][KPD][2 * gen_chunk(col >> 1, KPD) + (col & 1)] = make_float2(H, 1.f);
+            }
+        }
+    };
+
+    // acc[i][jj] = X_i . yt_j over the folded pair (first) and every coordinate pair of the
+    // tile in ys[buf]; KPT > 0 unrolls the k-pairs completely, so that every shared
+    // address is a register plus an immediate
+    const int kpd = KPD;
+    auto products = [&](int buf, u64 (&acc)[8][4]) {
+        const char *xs0 = reinterpret_cast<const char *>(&S.xs[0][tr * 8]);
+        const char *ys0 = reinterpret_cast<const char *>(&S.ys[buf][0][0]);
+        auto step = [&](int kp, bool first) {
+            const char *yp = ys0 + kp * (kBN * 8) + (gen_chunk(tc, kp) << 4);
+            const ulonglong2 y0 = *reinterpret_cast<const ulonglong2 *>(yp);
+            const ulonglong2 y1 = *reinterpret_cast<const ulonglong2 *>(yp + 256);
+            const u64 yv[4] = {y0.x, y0.y, y1.x, y1.y};
+            const char *xp = xs0 + kp * (kXS * 8);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const ulonglong2 x2 = *reinterpret_cast<const ulonglong2 *>(xp + 16 * h);
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    acc[2 * h][jj] = first ? mul2(x2.x, yv[jj]) : fma2(x2.x, yv[jj], acc[2 * h][jj]);
+                    acc[2 * h + 1][jj] = first ? mul2(x2.y, yv[jj]) : fma2(x2.y, yv[jj], acc[2 * h + 1][jj]);
+                }
+            }
+        };
+        step(kpd, true);  // acc = (H_j, -m_i)
+        if constexpr (KPT > 0) {
+#pragma unroll
+            for (int kp = 0; kp < KPT; ++kp) step(kp, false);
+        } else {
+#pragma unroll 1
+            for (int kp = 0; kp < KPD; kp += 2) {  // KPD is even (D4 is a multiple of 4)
+                step(kp, false);
+                step(kp + 1, false);
+            }
+        }
+    };
+
+    // one sweep over the column tiles; MAXP: per-row maximum of the exponent, else the sum
+    float res[8];
+    auto sweep = [&](bool MAXP) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) res[i] = MAXP ? -INFINITY : 0.f;
+        if (ntiles == 0) return;
+        int jc[2], jn[2];
+        load_idx(0, jc);
+        issue(0, jc);
+        cp_async_commit();
+        load_idx(1, jc);
+        issue(1, jc);
+        cp_async_commit();
+        load_idx(2, jn);
+        cp_async_wait1();
+        repack(0, 0);
+        __syncthreads();
+        for (int tt = 0; tt < ntiles; ++tt) {
+            const int buf = tt & 1;
+            if (tt + 2 < ntiles) issue(buf, jn);  // raw[buf] (tile tt) was repacked already
+            cp_async_commit();
+            load_idx(tt + 3, jn);
+            u64 acc[8][4];
+            products(buf, acc);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float e[4];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    float lo, hi;
+                    unpack2(acc[i][jj], lo, hi);
+                    e[jj] = lo + hi;
+                }
+                if (MAXP) res[i] = fmaxf(res[i], fmaxf(fmaxf(e[0], e[1]), fmaxf(e[2], e[3])));
+                else res[i] += (ex2(e[0]) + ex2(e[1])) + (ex2(e[2]) + ex2(e[3]));
+            }
+            if (tt + 1 < ntiles) {
+                cp_async_wait1();  // this thread's copies of tile tt+1
+                repack(buf ^ 1, tt + 1);
+            }
+            __syncthreads();
+        }
+        cp_async_wait0();
     };
 
     if constexpr (TWO) {
-        float mx[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) mx[i] = -INFINITY;
-        for (int tt = 0; tt < ntiles; ++tt) {
-            stage(tt * kBN);
-            float acc[8][4];
-            const float4 h4 = *reinterpret_cast<const float4 *>(&S.hs[tc * 4]);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { acc[i][0] = h4.x; acc[i][1] = h4.y; acc[i][2] = h4.z; acc[i][3] = h4.w; }
-            dots(acc);
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                mx[i] = fmaxf(mx[i], fmaxf(fmaxf(acc[i][0], acc[i][1]), fmaxf(acc[i][2], acc[i][3])));
-        }
+        sweep(true);
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-            for (int o = 8; o > 0; o >>= 1) mx[i] = fmaxf(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], o));
+            for (int o = 8; o > 0; o >>= 1) res[i] = fmaxf(res[i], __shfl_xor_sync(0xffffffffu, res[i], o));
         __syncthreads();
         if (tc == 0)
 #pragma unroll
-            for (int i = 0; i < 8; ++i) S.mrow[tr * 8 + i] = mx[i] > -INFINITY ? mx[i] : 0.f;
-        __syncthreads();
+            for (int i = 0; i < 8; ++i) S.xs[kpd][tr * 8 + i].y = res[i] > -INFINITY ? -res[i] : 0.f;
     }
-
-    float mreg[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) mreg[i] = S.mrow[tr * 8 + i];
-    float rs[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) rs[i] = 0.f;
-    for (int tt = 0; tt < ntiles; ++tt) {
-        stage(tt * kBN);
-        float acc[8][4];
-        const float4 h4 = *reinterpret_cast<const float4 *>(&S.hs[tc * 4]);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            acc[i][0] = h4.x - mreg[i]; acc[i][1] = h4.y - mreg[i];
-            acc[i][2] = h4.z - mreg[i]; acc[i][3] = h4.w - mreg[i];
-        }
-        dots(acc);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) rs[i] += (ex2(acc[i][0]) + ex2(acc[i][1])) + (ex2(acc[i][2]) + ex2(acc[i][3]));
-    }
-    // reduce the 16 column-threads of each row group (lanes of one half-warp)
+    __syncthreads();
+    sweep(false);
+    // reduce the 16 column-threads of each row group (lanes of one half-warp); lane tc < 8
+    // then finishes row 8 tr + tc
 #pragma unroll
     for (int i = 0; i < 8; ++i)
-        for (int o = 8; o > 0; o >>= 1) rs[i] += __shfl_xor_sync(0xffffffffu, rs[i], o);
-    float dmax = 0.f;
-    if (tc == 0) {
+        for (int o = 8; o > 0; o >>= 1) res[i] += __shfl_xor_sync(0xffffffffu, res[i], o);
+    float a = res[0];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int rr = tr * 8 + i;
-            if (rr >= nr) continue;
-            const int r = r0 + rr;
-            const float a = rs[i];
-            if (!row_sum_ok(a)) {
-                push_fallback(L, item.x, r, blk);
-                continue;
-            }
-            finish_row(L, I, r, (double)mreg[i] + log2((double)a), (double)S.hx[rr], dmax);
-        }
+    for (int i = 1; i < 8; ++i) a = (tc == i) ? res[i] : a;
+    float dmax = 0.f;
+    const int rr = tr * 8 + tc;
+    if (tc < 8 && rr < nr) {
+        const int r = r0 + rr;
+        const float mi = -S.xs[kpd][rr].y;
+        if (!row_sum_ok(a)) push_fallback(L, item.x, r, blk);
+        else finish_row(L, I, r, (double)mi + log2((double)a), (double)S.hx[rr], dmax);
     }
     dmax = block_max<kNTg>(dmax, S.red);
     if (t == 0) {
@@ -797,19 +903,23 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
         const int D4 = (D + 3) & ~3;
         static bool attr = false;
         if (!attr) {
-            OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)sizeof(GenSmem)));
-            OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)sizeof(GenSmem)));
+            const int bytes = (int)sizeof(GenSmem);
+            OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+            OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<false, 30>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+            OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+            OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
             attr = true;
         }
         if (two) {
-            softmin_gen_kernel<true><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
+            softmin_gen_kernel<true, 0><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
             OTGB_CHECK_LAUNCH();
         } else if (L.use_tc && D >= 16) {
             softmin_tc_launch(L, D, st);
         } else {
-            softmin_gen_kernel<false><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
+            // the k-pair loop unrolled at compile time for 60- and 64-wide points
+            if (D4 == 60) softmin_gen_kernel<false, 30><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
+            else if (D4 == 64) softmin_gen_kernel<false, 32><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
+            else softmin_gen_kernel<false, 0><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
             OTGB_CHECK_LAUNCH();
         }
     }
