@@ -133,7 +133,7 @@ struct SoftminLaunch {
     int exact_max;           // 1: take each row's shift from an exact maximum pass even when old values exist
     int use_tc;              // 1: D >= 16 cross term on the tensor cores (BF16 hi/lo split, FP32 accumulate)
     int use_tc3;             // 1: D <= 3 exponent on the tensor cores (three-piece BF16, float32 accuracy)
-    unsigned int *tc_err;    // set when a bounded tensor-core wait gave up (may be null)
+    unsigned int *tc_err;    // set when a bounded wait (tensor core or tile barrier) gave up (may be null)
     const int4 *fin;         // finalize list (split mode)
     int n_fin;
     const int *item_fin;     // split mode, optional: fin entry of each item; with fin_count the warp that

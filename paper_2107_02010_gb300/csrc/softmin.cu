@@ -519,7 +519,25 @@ struct GenSmem {
     float cen[64];
     float hx[kBM];           // |xt|^2 / 2
     float red[kNTg / 32];
+    unsigned long long tbar;  // tile barrier (mbarrier, kNTg arrivals per phase)
 };
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"((uint32_t)__cvta_generic_to_shared(bar))
+                 : "memory");
+}
+// true when the phase with the given parity completed within the iteration limit
+__device__ __forceinline__ bool mbar_wait_parity(unsigned long long *bar, uint32_t parity) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+    return done != 0;
+}
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -559,6 +577,12 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
     const float eps = L.eps, s = L.s;
     OTGB_DCLAMP(D4, 4, 65);
     const int KPD = KPT > 0 ? KPT : (D4 >> 1);  // coordinate pairs; pair KPD is the folded one
+
+    if (t == 0)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(&S.tbar)),
+                     "r"(kNTg));
+    uint32_t tphase = 0u;
+    bool timed_out = false;
 
     // ---- rows: raw pairs, centre (mean), X = s (x - c), |xt|^2 / 2, fold pair
     float *xsf = reinterpret_cast<float *>(&S.xs[0][0]);
@@ -726,6 +750,13 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
             load_idx(tt + 3, jn);
             u64 acc[8][4];
             products(buf, acc);
+            if (tt + 1 < ntiles) {
+                cp_async_wait1();  // this thread's copies of tile tt+1
+                repack(buf ^ 1, tt + 1);
+            }
+            // tile barrier split in two: arrive once ys[buf] is read and ys[buf ^ 1]
+            // written, fold the accumulators into the row sums, then wait
+            mbar_arrive(&S.tbar);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 float e[4];
@@ -738,11 +769,8 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
                 if (MAXP) res[i] = fmaxf(res[i], fmaxf(fmaxf(e[0], e[1]), fmaxf(e[2], e[3])));
                 else res[i] += (ex2(e[0]) + ex2(e[1])) + (ex2(e[2]) + ex2(e[3]));
             }
-            if (tt + 1 < ntiles) {
-                cp_async_wait1();  // this thread's copies of tile tt+1
-                repack(buf ^ 1, tt + 1);
-            }
-            __syncthreads();
+            if (!mbar_wait_parity(&S.tbar, tphase)) timed_out = true;
+            tphase ^= 1u;
         }
         cp_async_wait0();
     };
@@ -780,6 +808,7 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
         if (L.delta_max) atomicMax(L.delta_max, __float_as_uint(dmax));
         if (L.pairs) atomicAdd(L.pairs, (unsigned long long)nr * (unsigned long long)ncol);
     }
+    if (timed_out && L.tc_err) atomicOr(L.tc_err, 2u);
 }
 
 // ------------------------------------------------------------- fallback ---
