@@ -497,10 +497,11 @@ __global__ void __launch_bounds__(32 * kW3) softmin3_finalize_kernel(const __gri
 // instructions of the scalar form.
 //
 // Column tiles flow through a two-stage pipeline without register staging:
-// cp.async copies the raw coordinates (and log w_j, pot_j) of tile t+2 into
+// cp.async copies the raw coordinates (and log w_j, pot_j) of tile t+1 into
 // shared memory while the CTA multiplies tile t; after the products each
 // thread centres and repacks the part of tile t+1 that it copied itself (so
-// the copy needs no barrier), then one barrier per tile.  The column operand
+// the copy needs no barrier), issues the copies of tile t+2 into the slots it
+// just read, and meets the others at one barrier per tile.  The column operand
 // is stored with its 16-byte chunks XOR-swizzled by the k-pair, so both the
 // repacking stores and the operand loads are free of bank conflicts.
 // TWO = true: an exact-maximum first pass gives each row's shift.
@@ -513,9 +514,9 @@ constexpr int kXS = kBM + 2;  // float2 stride of a k-pair of X (spreads the sta
 struct GenSmem {
     float2 xs[kKP][kXS];     // X pairs; pair KPD = (1, -m_i)
     float2 ys[2][kKP][kBN];  // yt pairs, chunk-swizzled; pair KPD = (H_j, 1)
-    float raw[2][kBN][64];   // raw column coordinates, as copied
-    float rlw[2][kBN];
-    float rpot[2][kBN];
+    float raw[kBN][64];      // raw column coordinates of the next tile, as copied
+    float rlw[kBN];
+    float rpot[kBN];
     float cen[64];
     float hx[kBM];           // |xt|^2 / 2
     float red[kNTg / 32];
@@ -642,7 +643,7 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
             j[q] = jj;
         }
     };
-    auto issue = [&](int buf, const int (&j)[2]) {
+    auto issue = [&](const int (&j)[2]) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int col = colb + 32 * q;
@@ -650,15 +651,16 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
             // a copy of size 0 fills zeros and reads nothing; its source is then the valid base
             const bool k0 = ok && 8 * ch + 4 <= D4, k1 = ok && 8 * ch + 8 <= D4;
             const float *src = I.cols + (ok ? (size_t)j[q] * D4 + 8 * ch : 0);
-            cp_async16(&S.raw[buf][col][8 * ch], k0 ? src : I.cols, k0 ? 16 : 0);
-            cp_async16(&S.raw[buf][col][8 * ch + 4], k1 ? src + 4 : I.cols, k1 ? 16 : 0);
+            cp_async16(&S.raw[col][8 * ch], k0 ? src : I.cols, k0 ? 16 : 0);
+            cp_async16(&S.raw[col][8 * ch + 4], k1 ? src + 4 : I.cols, k1 ? 16 : 0);
             if (ch == 0) {
-                cp_async4(&S.rlw[buf][col], ok ? I.col_logw + j[q] : I.col_logw, ok ? 4 : 0);
-                cp_async4(&S.rpot[buf][col], ok ? I.col_pot + j[q] : I.col_pot, ok ? 4 : 0);
+                cp_async4(&S.rlw[col], ok ? I.col_logw + j[q] : I.col_logw, ok ? 4 : 0);
+                cp_async4(&S.rpot[col], ok ? I.col_pot + j[q] : I.col_pot, ok ? 4 : 0);
             }
         }
     };
-    // centre and repack the part of tile `tile` this thread copied into raw[buf]
+    // centre and repack into ys[buf] the part of tile `tile` this thread copied into raw
+    // (a column past the end has H = -inf, which zeroes its terms whatever its coordinates)
     auto repack = [&](int buf, int tile) {
         const float4 ca = *reinterpret_cast<const float4 *>(&S.cen[8 * ch]);
         const float4 cc = *reinterpret_cast<const float4 *>(&S.cen[8 * ch + 4]);
@@ -666,15 +668,12 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
         for (int q = 0; q < 2; ++q) {
             const int col = colb + 32 * q;
             const bool ok = tile * kBN + col < ncol;
-            const float4 a = *reinterpret_cast<const float4 *>(&S.raw[buf][col][8 * ch]);
-            const float4 b = *reinterpret_cast<const float4 *>(&S.raw[buf][col][8 * ch + 4]);
+            const float4 a = *reinterpret_cast<const float4 *>(&S.raw[col][8 * ch]);
+            const float4 b = *reinterpret_cast<const float4 *>(&S.raw[col][8 * ch + 4]);
             float v[8] = {a.x - ca.x, a.y - ca.y, a.z - ca.z, a.w - ca.w, b.x - cc.x, b.y - cc.y, b.z - cc.z, b.w - cc.w};
             float sq = 0.f;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                v[e] = ok ? v[e] : 0.f;
-                sq = fmaf(v[e], v[e], sq);
-            }
+            for (int e = 0; e < 8; ++e) sq = fmaf(v[e], v[e], sq);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int kp = 4 * ch + e;
@@ -684,7 +683,7 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
             sq += __shfl_xor_sync(0xffffffffu, sq, 2);
             sq += __shfl_xor_sync(0xffffffffu, sq, 4);
             if (ch == 0) {
-                const float H = ok ? s * (fmaf(eps, S.rlw[buf][col], S.rpot[buf][col]) - 0.5f * sq) : -INFINITY;
+                const float H = ok ? s * (fmaf(eps, S.rlw[col], S.rpot[col]) - 0.5f * sq) : -INFINITY;
                 S.ys[buf][KPD][2 * gen_chunk(col >> 1, KPD) + (col & 1)] = make_float2(H, 1.f);
             }
         }
@@ -732,27 +731,27 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
 #pragma unroll
         for (int i = 0; i < 8; ++i) res[i] = MAXP ? -INFINITY : 0.f;
         if (ntiles == 0) return;
-        int jc[2], jn[2];
-        load_idx(0, jc);
-        issue(0, jc);
+        int jn[2];
+        load_idx(0, jn);
+        issue(jn);
         cp_async_commit();
-        load_idx(1, jc);
-        issue(1, jc);
+        load_idx(1, jn);
+        cp_async_wait0();
+        repack(0, 0);
+        issue(jn);  // tile 1 (nothing past the end)
         cp_async_commit();
         load_idx(2, jn);
-        cp_async_wait1();
-        repack(0, 0);
         __syncthreads();
         for (int tt = 0; tt < ntiles; ++tt) {
             const int buf = tt & 1;
-            if (tt + 2 < ntiles) issue(buf, jn);  // raw[buf] (tile tt) was repacked already
-            cp_async_commit();
-            load_idx(tt + 3, jn);
             u64 acc[8][4];
             products(buf, acc);
             if (tt + 1 < ntiles) {
-                cp_async_wait1();  // this thread's copies of tile tt+1
+                cp_async_wait0();  // this thread's copies of tile tt+1
                 repack(buf ^ 1, tt + 1);
+                if (tt + 2 < ntiles) issue(jn);  // into the raw slots just consumed
+                cp_async_commit();
+                load_idx(tt + 3, jn);
             }
             // tile barrier split in two: arrive once ys[buf] is read and ys[buf ^ 1]
             // written, fold the accumulators into the row sums, then wait
