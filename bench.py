@@ -77,8 +77,8 @@ def params_for(args, otgb):
 
 def start_clock_sampler():
     try:
-        f = open(os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                 else os.devnull, "w")
+        # the raw samples go to the file named by OTGB_CLOCKS_CSV, if set
+        f = open(os.environ.get("OTGB_CLOCKS_CSV") or os.devnull, "w")
         p = subprocess.Popen(
             ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"

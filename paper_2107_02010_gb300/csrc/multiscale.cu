@@ -369,6 +369,7 @@ int Multiscale::run_schedule(Solver &s, const otgb_params &P, const std::vector<
     OTGB_CUDA_TRY(cudaMemcpyAsync(d_clx, hclx.data(), sizeof(int) * hclx.size(), cudaMemcpyHostToDevice, st));
     OTGB_CUDA_TRY(cudaMemcpyAsync(d_cly, hcly.data(), sizeof(int) * hcly.size(), cudaMemcpyHostToDevice, st));
     s.setup_instances(hbx, hby);
+    setup_tcc(s);
 
     // coarse phase on the cluster measures while sigma > sigma_switch
     size_t k = 0;
@@ -403,6 +404,7 @@ int Multiscale::run_schedule(Solver &s, const otgb_params &P, const std::vector<
         const double sig = k < sched.size() ? sched[k] : P.blur;
         const double eps = sig * sig;
         SoftminLaunch E = s.launch;  // fallback buffers, counters
+        E.use_tcc = 0;
         E.eps = (float)eps;
         E.s = (float)(1.4426950408889634 / eps);
         E.eps_ln2 = eps * 0.69314718055994530942;
@@ -496,6 +498,10 @@ void Multiscale::before_fine_step(Solver &s, double sigma) {
     }
     mask_kernel<<<dim3(ncmax, 4), 256, 0, st>>>(M);
     OTGB_CHECK_LAUNCH();
+    if (s.launch.use_tcc) {
+        require(nwords == s.launch.tcc_nwords, "before_fine_step: keep-bit words changed", OTGB_EINTERNAL);
+        for (int q = 0; q < 4; ++q) s.launch.inst[q].tcc_bits = M.inst[q].bits;
+    }
     // column lists per (instance, block): count, host prefix, write
     ListLaunch LL;
     std::memset(&LL, 0, sizeof(LL));
@@ -541,6 +547,66 @@ void Multiscale::before_fine_step(Solver &s, double sigma) {
     }
     last_kept_fraction = dense > 0 ? kept / dense : 1.0;
     s.set_work(ncols, D <= 3);
+}
+
+void Multiscale::setup_tcc(Solver &s) {
+    const int D4 = s.X.stride;
+    const int nwords = (std::max(ncl_x, ncl_y) + 31) / 32;
+    s.launch.use_tcc = 0;
+    if (!s.use_tc || s.D <= 3 || D4 > 60 || nwords > kTccMaxWords) return;
+    cudaStream_t st = s.st;
+    Workspace &ws = *s.ws;
+    struct Side {
+        int *tile0, *tile_cl;
+        int ntiles;
+        unsigned char *copy[2];
+        float *half_norm;
+    } side[2];
+    const std::vector<int> *offs[2] = {&s.X_off, &s.Y_off};
+    const char *tag[2] = {"x", "y"};
+    for (int k = 0; k < 2; ++k) {
+        const std::vector<int> &off = *offs[k];
+        const int ncl = (int)off.size() - 1;
+        std::vector<int> t0(ncl + 1), tcl;
+        t0[0] = 0;
+        for (int J = 0; J < ncl; ++J) {
+            const int nt = (off[J + 1] - off[J] + 127) / 128;
+            for (int q = 0; q < nt; ++q) tcl.push_back(J);
+            t0[J + 1] = t0[J] + nt;
+        }
+        Side &S = side[k];
+        S.ntiles = t0[ncl];
+        S.tile0 = ws.get<int>(std::string("tcc:t0") + tag[k], ncl + 1);
+        S.tile_cl = ws.get<int>(std::string("tcc:tcl") + tag[k], std::max(S.ntiles, 1));
+        OTGB_CUDA_TRY(cudaMemcpyAsync(S.tile0, t0.data(), sizeof(int) * (ncl + 1), cudaMemcpyHostToDevice, st));
+        if (S.ntiles)
+            OTGB_CUDA_TRY(cudaMemcpyAsync(S.tile_cl, tcl.data(), sizeof(int) * S.ntiles, cudaMemcpyHostToDevice, st));
+        const size_t bytes = (size_t)std::max(S.ntiles, 1) * tcc_tile_bytes();
+        S.copy[0] = static_cast<unsigned char *>(ws.get(std::string("tcc:tiles0") + tag[k], bytes));
+        S.copy[1] = static_cast<unsigned char *>(ws.get(std::string("tcc:tiles1") + tag[k], bytes));
+        S.half_norm = ws.get<float>(std::string("tcc:hn") + tag[k], (size_t)std::max(S.ntiles, 1) * 128);
+        tcc_build_side(k == 0 ? s.X.pts : s.Y.pts, D4, k == 0 ? d_off_x : d_off_y, S.tile0, S.tile_cl, S.ntiles,
+                       k == 0 ? cen_x : cen_y, S.copy[0], S.copy[1], S.half_norm, st);
+        OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors go out of scope
+    }
+    // instance 0: rows x, cols x; 1: rows y, cols y; 2: rows y, cols x; 3: rows x, cols y
+    const int colside[4] = {0, 1, 0, 1}, copy[4] = {0, 0, 1, 1};
+    const int *blk_cl[4] = {d_clx, d_cly, d_cly, d_clx};
+    for (int q = 0; q < 4; ++q) {
+        SoftminInst &I = s.launch.inst[q];
+        const Side &S = side[colside[q]];
+        I.tcc_tiles = S.copy[copy[q]];
+        I.tcc_half_norm = S.half_norm;
+        I.tcc_tile0 = S.tile0;
+        I.tcc_tile_cl = S.tile_cl;
+        I.tcc_ntiles = S.ntiles;
+        I.tcc_coff = colside[q] == 0 ? d_off_x : d_off_y;
+        I.tcc_ccen = colside[q] == 0 ? cen_x : cen_y;
+        I.tcc_bits = nullptr;  // set with every new mask
+        I.tcc_blk_cl = blk_cl[q];
+    }
+    s.launch.tcc_nwords = nwords;
+    s.launch.use_tcc = 1;
 }
 
 }  // namespace otgb

@@ -112,6 +112,9 @@ struct Multiscale {
                  const std::vector<float> &hiy, float *d_box);
     int run_schedule(Solver &s, const otgb_params &P, const std::vector<double> &sched, int block_rows);
     void before_fine_step(Solver &s, double sigma);
+    // the column tiles of the cluster-tiled tensor-core form, when it applies (tensor-core precision,
+    // D4 <= 60, at most 32 x kTccMaxWords clusters per side)
+    void setup_tcc(Solver &s);
 };
 
 }  // namespace otgb

@@ -109,9 +109,25 @@ struct SoftminInst {
     const int *blk_row0;
     const int *col_ptr;
     const int *col_list;
+    // Cluster-tiled tensor-core form (softmin_tcc.cu, coarse-to-fine solves): the column side's points
+    // centred at their cluster's centre and split into BF16 tiles of 128 columns (tcc_tiles, 32 KiB per
+    // tile: hi then lo, with H_j in K slots 60..63 rewritten every step); tile0[J] .. tile0[J+1] are the
+    // tiles of column cluster J (tile_cl: the cluster of each tile); half_norm: |y_j - c_J|^2 / 2 per tile
+    // column; coff / ccen: column cluster offsets and centres; bits / blk_cl: keep bits of the row clusters
+    // (tcc_nwords words each) and the row clusters of each block.
+    const unsigned char *tcc_tiles;
+    const float *tcc_half_norm;
+    const int *tcc_tile0;
+    const int *tcc_tile_cl;
+    int tcc_ntiles;
+    const int *tcc_coff;
+    const float *tcc_ccen;
+    const unsigned *tcc_bits;
+    const int *tcc_blk_cl;
 };
 
 constexpr int kMaxInst = 4;
+constexpr int kTccMaxWords = 256;  // column clusters of the cluster-tiled form: at most 32 x 256
 
 // Work decomposition: one item (inst, blk, cb, ce) = the rows of block blk of
 // instance inst against the positions [cb, ce) of the block's column sequence;
@@ -133,6 +149,8 @@ struct SoftminLaunch {
     int exact_max;           // 1: take each row's shift from an exact maximum pass even when old values exist
     int use_tc;              // 1: D >= 16 cross term on the tensor cores (BF16 hi/lo split, FP32 accumulate)
     int use_tc3;             // 1: D <= 3 exponent on the tensor cores (three-piece BF16, float32 accuracy)
+    int use_tcc;             // 1 (with use_tc): the cluster-tiled tensor-core form (tcc_* fields of the instances)
+    int tcc_nwords;          // words of keep bits per row cluster
     unsigned int *tc_err;    // set when a bounded wait (tensor core or tile barrier) gave up (may be null)
     const int4 *fin;         // finalize list (split mode)
     int n_fin;
@@ -161,6 +179,17 @@ void softmin_tc_launch(const SoftminLaunch &L, int D, cudaStream_t st);
 // blocks <= 128 rows, split blocks only with item_fin / fin_count.
 void softmin3_tc_launch(const SoftminLaunch &L, cudaStream_t st);
 size_t softmin_tc_smem_bytes();
+// Cluster-tiled tensor-core softmin (softmin_tcc.cu): D4 <= 60, old values required, one item per block.
+void softmin_tcc_launch(const SoftminLaunch &L, int D, cudaStream_t st);
+// Bytes of one column tile of the cluster-tiled form (128 columns, hi and lo pieces).
+size_t tcc_tile_bytes();
+// Column tiles of one side (points pts with stride D4, cluster offsets / first tiles / tile clusters and
+// centres on the device), written into two copies (one per instance that uses this side as columns).
+void tcc_build_side(const float *pts, int D4, const int *d_off, const int *d_tile0, const int *d_tile_cl,
+                    int ntiles, const float *cen, unsigned char *dst0, unsigned char *dst1, float *half_norm,
+                    cudaStream_t st);
+// H_j of the current step into the column tiles of every instance of L (uses col_pot, col_logw, s, eps).
+void tcc_update(const SoftminLaunch &L, cudaStream_t st);
 
 // Build uniform row blocks of `block_rows` rows for an instance of n rows:
 // writes blk_row0 (n_blocks+1) on the device.  Returns n_blocks.

@@ -116,6 +116,7 @@ void Solver::step(double sigma, bool count_pairs) {
         harvest_timing();
     }
     if (timing) OTGB_CUDA_TRY(cudaEventRecord(ev_pool[2 * ev_used], st));
+    if (L.use_tcc) tcc_update(L, st);
     softmin_run(L, D, rows_per_thread, st);
     if (timing) {
         OTGB_CUDA_TRY(cudaEventRecord(ev_pool[2 * ev_used + 1], st));

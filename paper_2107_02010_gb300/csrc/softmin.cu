@@ -942,7 +942,8 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
             softmin_gen_kernel<true, 0><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
             OTGB_CHECK_LAUNCH();
         } else if (L.use_tc && D >= 16) {
-            softmin_tc_launch(L, D, st);
+            if (L.use_tcc) softmin_tcc_launch(L, D, st);
+            else softmin_tc_launch(L, D, st);
         } else {
             // the k-pair loop unrolled at compile time for 60- and 64-wide points
             if (D4 == 60) softmin_gen_kernel<false, 30><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);

@@ -99,7 +99,7 @@ def test_multiscale_kmeans_fibers_matches_dense_gpu(ctx):
     # one slowly contracting translation mode per bundle; float32 rounding of the
     # 60-D dot products is amplified ~1/(1 - (1 + lambda)/2) = 200 times along
     # them, so two float32 runs differ by up to ~1e-4 in the duals while S, which
-    # does not see these modes, agrees to ~1e-7 (error budget).
+    # does not see these modes, agrees to ~1e-7.
     for k in ("f", "g", "a_self", "b_self"):
         err = rel(ms[k], dense[k].cpu().numpy().astype(np.float64), eps)
         print(k, err)

@@ -73,3 +73,45 @@ def test_tensorcore_converged_labels(ctx):
     top2 = np.sort(rsc, axis=1)[:, -2:]
     clear = top2[:, 1] - top2[:, 0] >= 1e-4 * top2[:, 1]
     assert np.all(am.cpu().numpy()[clear] == ram[clear])
+
+
+@pytest.mark.parametrize("P", [20, 7])
+def test_tensorcore_cluster_tiles_match_fp32_and_oracle_rows(ctx, P):
+    """The cluster-tiled form of the coarse-to-fine solve (the column operand centred at its k-means
+    cluster's centre, split once per solve, H_j refreshed every step; P = 20 gives D = 60, P = 7 gives
+    D = 21, D4 = 24): S and the duals against the float32 solve of the same problem to the reduced-precision
+    bar, sampled rows of the duals against the FP64 oracle's dense softmin (the fixed point, up to the last
+    step and the truncation), S against the oracle's FP64 sums of the same duals."""
+    from paper_2107_02010_gb300 import otgb
+
+    ctrl = synth.bundle_centrelines(P=P)
+    x, a, _ = synth.fiber_bundles(6000, seed=4, ctrl=ctrl, P=P, perturb=3.0)
+    y, b, _ = synth.fiber_bundles(5000, seed=5, ctrl=ctrl, P=P)
+    blur, reach = 2.0, 20.0
+    common = dict(blur=blur, reach=reach, scaling=0.5, multiscale=1, cluster=1, k_clusters=30, kmeans_iters=10,
+                  tol=1e-7, max_iters=20000)
+    r32 = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b), otgb.default_params(precision=0, **common),
+                                   want_self=True)
+    rtc = otgb.sinkhorn_divergence(ctx, T(x), T(a), T(y), T(b), otgb.default_params(precision=1, **common),
+                                   want_self=True)
+    print("fp32", r32["stats"], "\ntc", rtc["stats"])
+    assert rtc["status"] == 0 and rtc["stats"]["kept_fraction"] < 0.9
+    eps = blur ** 2
+    assert abs(rtc["S"] - r32["S"]) <= TOL_TC * abs(r32["S"]), (rtc["S"], r32["S"])
+    for k in ("f", "g", "a_self", "b_self"):
+        err = rel(rtc[k], r32[k].cpu().numpy().astype(np.float64), eps)
+        print(k, err)
+        assert err < TOL_TC, k
+    d = [rtc[k].cpu().numpy().astype(np.float64) for k in ("a_self", "b_self", "f", "g")]
+    S_ref = oracle.divergence(a, b, eps, oracle.rho(reach), *d)
+    assert abs(rtc["S"] - S_ref) <= 1e-9 * abs(S_ref)
+    f, g = d[2], d[3]
+    lam = oracle.lam(blur, reach)
+    delta = rtc["stats"]["last_delta"]
+    rng = np.random.default_rng(9)
+    ix = np.sort(rng.choice(len(x), 64, replace=False))
+    iy = np.sort(rng.choice(len(y), 64, replace=False))
+    for name, q, pts, w, pot, got in (("f", x[ix], y, b, g, f[ix]), ("g", y[iy], x, a, f, g[iy])):
+        ref = oracle.softmin(q, pts, w, pot, eps, lam)
+        err = np.abs(got - ref)
+        assert np.all(err <= 3.0 * delta * eps + TOL_TC * (np.abs(ref) + eps)), (name, float(err.max()))
