@@ -811,18 +811,23 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
 }
 
 // ------------------------------------------------------------- fallback ---
-// Rows flagged by the fast kernels, one warp per row (grid-stride over the
+// Rows flagged by the fast kernels, one CTA per row (grid-stride over the
 // device-side count, so the launch needs no host synchronisation): two passes
 // over the row's columns in the direct form -|x - y|^2/2 (no cancellation),
-// max first, then the shifted sum.
-__global__ void softmin_fallback_kernel(const __grid_constant__ SoftminLaunch L, int D, int stride) {
+// max first, then the shifted sum in double.
+constexpr int kFbThreads = 256;
+
+__global__ void __launch_bounds__(kFbThreads) softmin_fallback_kernel(const __grid_constant__ SoftminLaunch L, int D,
+                                                                      int stride) {
+    __shared__ __align__(16) float xs[64];
+    __shared__ float redf[kFbThreads / 32];
+    __shared__ double redd[kFbThreads / 32];
     const int count = min(*L.n_fallback, L.fallback_cap);
     if (blockIdx.x == 0 && threadIdx.x == 0 && L.fallback_total && count > 0)
         atomicAdd(L.fallback_total, (unsigned long long)count);
-    const int lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += nw) {
-        int4 fb = L.fallback[w];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        int4 fb = L.fallback[q];
         OTGB_DCLAMP(fb.x, 0, L.n_inst);
         const SoftminInst &I = L.inst[fb.x];
         OTGB_DCLAMP(fb.y, 0, I.n_rows);
@@ -830,25 +835,51 @@ __global__ void softmin_fallback_kernel(const __grid_constant__ SoftminLaunch L,
         const int *list = I.col_list;
         int c0 = 0, c1 = I.n_cols;
         if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
-        const float *xi = I.rows + (size_t)r * stride;
+        __syncthreads();  // the previous row is done with xs and the reductions
+        if (t < stride) xs[t] = I.rows[(size_t)r * stride + t];
+        __syncthreads();
         const float eps = L.eps, s = L.s;
+        const int n4 = stride >> 2;
         auto term = [&](int p) -> float {
             int j = list ? list[c0 + p] : p;
             OTGB_DCLAMP(j, 0, I.n_cols);
-            const float *yj = I.cols + (size_t)j * stride;
-            float d2 = 0.f;
-            for (int k = 0; k < D; ++k) { const float t = xi[k] - yj[k]; d2 = fmaf(t, t, d2); }
-            const float lw = (D <= 3) ? yj[3] : I.col_logw[j];
+            const float4 *yj = reinterpret_cast<const float4 *>(I.cols + (size_t)j * stride);
+            float d2 = 0.f, lw;
+            if (D <= 3) {
+                const float4 v = yj[0];
+                const float t0 = xs[0] - v.x, t1 = D > 1 ? xs[1] - v.y : 0.f, t2 = D > 2 ? xs[2] - v.z : 0.f;
+                d2 = fmaf(t0, t0, fmaf(t1, t1, t2 * t2));
+                lw = v.w;
+            } else {
+                // coordinates past D are zero on both sides
+                for (int k4 = 0; k4 < n4; ++k4) {
+                    const float4 v = yj[k4];
+                    const float4 u = *reinterpret_cast<const float4 *>(&xs[4 * k4]);
+                    const float t0 = u.x - v.x, t1 = u.y - v.y, t2 = u.z - v.z, t3 = u.w - v.w;
+                    d2 = fmaf(t0, t0, fmaf(t1, t1, fmaf(t2, t2, fmaf(t3, t3, d2))));
+                }
+                lw = I.col_logw[j];
+            }
             return s * (fmaf(eps, lw, I.col_pot[j]) - 0.5f * d2);
         };
+        const int n = c1 - c0;
         float m = -INFINITY;
-        for (int p = lane; p < c1 - c0; p += 32) m = fmaxf(m, term(p));
+        for (int p = t; p < n; p += kFbThreads) m = fmaxf(m, term(p));
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) redf[wid] = m;
+        __syncthreads();
+        m = redf[0];
+#pragma unroll
+        for (int k = 1; k < kFbThreads / 32; ++k) m = fmaxf(m, redf[k]);
         double acc = 0.0;
         if (m > -INFINITY)
-            for (int p = lane; p < c1 - c0; p += 32) acc += (double)exp2f(term(p) - m);
+            for (int p = t; p < n; p += kFbThreads) acc += (double)exp2f(term(p) - m);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
+        if (lane == 0) redd[wid] = acc;
+        __syncthreads();
+        if (t == 0) {
+            acc = 0.0;
+            for (int k = 0; k < kFbThreads / 32; ++k) acc += redd[k];
             float dmax = 0.f;
             const double L2 = (m > -INFINITY) ? (double)m + log2(acc) : -INFINITY;
             finish_row(L, I, r, L2, 0.0, dmax);
@@ -893,6 +924,19 @@ void launch_softmin3(const SoftminLaunch &L, cudaStream_t st) {
     softmin3_kernel<R, TWO><<<grid, 32 * kW3, 0, st>>>(L);
 }
 
+}  // namespace
+
+namespace {
+int fallback_grid_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        OTGB_CUDA_TRY(cudaGetDevice(&dev));
+        OTGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
 }  // namespace
 
 void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_t st) {
@@ -953,7 +997,7 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
         }
     }
     const int stride = D <= 3 ? 4 : ((D + 3) & ~3);
-    softmin_fallback_kernel<<<64, 256, 0, st>>>(L, D, stride);
+    softmin_fallback_kernel<<<2 * fallback_grid_sms(), kFbThreads, 0, st>>>(L, D, stride);
     OTGB_CHECK_LAUNCH();
 }
 

@@ -20,8 +20,9 @@
 //
 // One CTA (4 warps, one tensor-memory lane per row) owns a block of at most 128 rows.  Thread 0 issues the
 // bulk copies (two shared-memory stages of a 32 KiB tile: hi then lo) and the MMAs (two 128-column
-// accumulators), so that the MMA of tile k+1 runs while the CTA sums tile k.  Every wait is bounded; a
-// timeout sets an error word and the kernel still releases its tensor memory.
+// accumulators), so that the MMA of tile k+1 runs while the CTA sums tile k; the threads hand an
+// accumulator back through an mbarrier, so the only CTA barriers are the restagings of the row operand.
+// Every wait is bounded; a timeout sets an error word and the kernel still releases its tensor memory.
 #include <cfloat>
 #include <cmath>
 
@@ -43,7 +44,7 @@ struct TccSmem {
     unsigned char a[2][kPiece];        // row operand: hi, lo
     unsigned char b[2][kTile];         // two stages of column tiles
     unsigned words[kMaxWords];         // kept column clusters of this block
-    unsigned long long mb_tma[2], mb_mma[2];
+    unsigned long long mb_tma[2], mb_mma[2], mb_free[2];
     uint32_t tslot;
     int ncols;
 };
@@ -137,6 +138,8 @@ __global__ void __launch_bounds__(128, 2) softmin_tcc_kernel(const __grid_consta
         tc::mbar_init(&S.mb_tma[1], 1);
         tc::mbar_init(&S.mb_mma[0], 1);
         tc::mbar_init(&S.mb_mma[1], 1);
+        tc::mbar_init(&S.mb_free[0], kM);
+        tc::mbar_init(&S.mb_free[1], kM);
         tc::mbar_init_fence();
     }
     __syncthreads();
@@ -160,18 +163,26 @@ __global__ void __launch_bounds__(128, 2) softmin_tcc_kernel(const __grid_consta
     if (valid) Mi = (float)(-(double)s * (double)I.row_old[r0 + t] / (double)I.lam);
 
     // row operand for column cluster J: s (x - c_J) split hi / lo, R_iJ in slots 62, 63
+    const float4 *xr4 = reinterpret_cast<const float4 *>(xr);
     auto stage_rows = [&](int J) {
-        const float *cj = I.tcc_ccen + (size_t)J * D4;
+        const float4 *cj4 = reinterpret_cast<const float4 *>(I.tcc_ccen + (size_t)J * D4);
         float sq = 0.f;
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
             float v[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int k = 8 * ch + e;
-                const float d = (valid && k < D4) ? xr[k] - cj[k] : 0.f;
-                sq = fmaf(d, d, sq);
-                v[e] = s * d;
+            for (int h = 0; h < 2; ++h) {
+                const int k4 = 2 * ch + h;
+                float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (valid && 4 * k4 < D4) {
+                    const float4 a = xr4[k4], c = cj4[k4];
+                    d = make_float4(a.x - c.x, a.y - c.y, a.z - c.z, a.w - c.w);
+                }
+                sq = fmaf(d.x, d.x, fmaf(d.y, d.y, fmaf(d.z, d.z, fmaf(d.w, d.w, sq))));
+                v[4 * h] = s * d.x;
+                v[4 * h + 1] = s * d.y;
+                v[4 * h + 2] = s * d.z;
+                v[4 * h + 3] = s * d.w;
             }
             uint4 hi, lo;
             split8(v, hi, lo);
@@ -213,7 +224,8 @@ __global__ void __launch_bounds__(128, 2) softmin_tcc_kernel(const __grid_consta
     const unsigned char *tiles = I.tcc_tiles;
     bool ok = true;
     float tot = 0.f;
-    uint32_t ph_tma = 0u, ph_mma = 0u;  // bit b: parity of the next completion of stage / accumulator b
+    // bit b: parity of the next completion of stage b's copy / accumulator b's MMA / accumulator b's release
+    uint32_t ph_tma = 0u, ph_mma = 0u, ph_free = 0u;
     TileIt itL, itM;
     bool have = tile_next(itM, S.words, nwords, tile0);
     if (t == 0) {
@@ -253,6 +265,10 @@ __global__ void __launch_bounds__(128, 2) softmin_tcc_kernel(const __grid_consta
                 tc::fence_after();
             }
             if (t == 0) {
+                if (k >= 1) {  // every thread has read accumulator nb (tile k-1)
+                    if (!tc::mbar_wait(&S.mb_free[nb], (ph_free >> nb) & 1u)) ok = false;
+                    ph_free ^= 1u << nb;
+                }
                 if (!tc::mbar_wait(&S.mb_tma[nb], (ph_tma >> nb) & 1u)) ok = false;
                 ph_tma ^= 1u << nb;
                 tc::fence_after();
@@ -291,8 +307,10 @@ __global__ void __launch_bounds__(128, 2) softmin_tcc_kernel(const __grid_consta
             tc::ld_wait(vb);
             sum32(vb);
         }
+        // accumulator buf is read (released to the MMA issuer without a CTA barrier); stage buf is
+        // free, its MMA completed
         tc::fence_before();
-        __syncthreads();  // accumulator buf is read; stage buf is free (its MMA completed)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&S.mb_free[buf])) : "memory");
         if (t == 0 && tile_next(itL, S.words, nwords, tile0))
             tma_tile(S.b[buf], tiles + (size_t)itL.g * kTile, &S.mb_tma[buf]);
         itM = itN;
