@@ -278,6 +278,9 @@ __global__ void __launch_bounds__(128, 2) softmin_tcc_kernel(const __grid_consta
         // sums of tile k
         if (!tc::mbar_wait(&S.mb_mma[buf], (ph_mma >> buf) & 1u)) ok = false;
         ph_mma ^= 1u << buf;
+        // stage buf is free (MMA k completed): the copy of tile k+2 starts before the sums
+        if (t == 0 && tile_next(itL, S.words, nwords, tile0))
+            tma_tile(S.b[buf], tiles + (size_t)itL.g * kTile, &S.mb_tma[buf]);
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
         tc::fence_after();
         if (ok) {
@@ -307,12 +310,9 @@ __global__ void __launch_bounds__(128, 2) softmin_tcc_kernel(const __grid_consta
             tc::ld_wait(vb);
             sum32(vb);
         }
-        // accumulator buf is read (released to the MMA issuer without a CTA barrier); stage buf is
-        // free, its MMA completed
+        // accumulator buf is read: released to the MMA issuer without a CTA barrier
         tc::fence_before();
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&S.mb_free[buf])) : "memory");
-        if (t == 0 && tile_next(itL, S.words, nwords, tile0))
-            tma_tile(S.b[buf], tiles + (size_t)itL.g * kTile, &S.mb_tma[buf]);
         itM = itN;
         have = haveN;
         ++k;
