@@ -43,7 +43,11 @@ typedef enum {
 /* OTGB_FP32: float32 accuracy; for D <= 3 the exponent of every pair is one tensor-core dot
    product of three-piece BF16 operands (about 24 significant bits) with FP32 accumulation,
    elsewhere CUDA-core float32.  OTGB_TC_BF16X3: the reduced-precision tensor-core cross term
-   for D >= 16 (about 16 bits).  OTGB_FP32_SIMT: float32 on the CUDA cores for every D. */
+   for D >= 16 (about 16 bits); in coarse-to-fine solves with k-means clusters and
+   round_up(D, 4) <= 60 the column operand is centred at its cluster's centroid and split once
+   per solve, which holds 256 bytes per point and copy, two copies per side, in the context's
+   scratch (about 0.5 KB per point of x and of y; at most 8192 clusters per side).
+   OTGB_FP32_SIMT: float32 on the CUDA cores for every D. */
 typedef enum { OTGB_FP32 = 0, OTGB_TC_BF16X3 = 1, OTGB_FP32_SIMT = 2 } otgb_precision;
 typedef enum { OTGB_CLUSTER_GRID = 0, OTGB_CLUSTER_KMEANS = 1 } otgb_cluster_kind;
 
