@@ -124,21 +124,30 @@ def flush_l2(buf):
     buf.add_(1.0)  # touches 256 MB (> 129 MB L2)
 
 
-def cpu_baseline(x, a, y, b, rows=2048):
+def cpu_baseline(x, a, y, b, rows=0, target_s=10.0):
     """The FP64 oracle's softmin on a bounded sample: `rows` rows of the
-    alpha->beta instance against all columns, at eps = blur^2."""
+    alpha->beta instance against all columns, at eps = blur^2.  rows = 0: a
+    calibration run of 2048 rows sets the row count for about target_s seconds
+    (at most every row).  Returns (the cpu_baseline object, rows used)."""
     import oracle
 
     oracle.build()
-    idx = np.linspace(0, x.shape[0] - 1, rows).astype(np.int64)
     pot = np.zeros(y.shape[0])
-    t0 = time.perf_counter()
-    oracle.softmin(x[idx], y, b, pot, 1.0, 1.0 / 1.01)
-    dt = time.perf_counter() - t0
+
+    def run(n):
+        idx = np.linspace(0, x.shape[0] - 1, n).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.softmin(x[idx], y, b, pot, 1.0, 1.0 / 1.01)
+        return time.perf_counter() - t0
+
+    if rows <= 0:
+        dt0 = run(2048)
+        rows = int(min(x.shape[0], max(2048, 2048 * target_s / max(dt0, 1e-6))))
+    dt = run(rows)
     pairs = rows * y.shape[0]
     return {"value": pairs / dt, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "FP64 oracle softmin: %d rows x %d columns of the track-density workload (%.2f s)" %
-                      (rows, y.shape[0], dt)}
+            "sample": "FP64 oracle softmin: %d rows x %d columns of the track-density workload (%.1f s)" %
+                      (rows, y.shape[0], dt)}, rows
 
 
 def peak_pairs_per_s(D, clock_mhz, n_sm):
@@ -260,8 +269,9 @@ def run_reference(args):
     x, a, y, b = workload(args)
     cb = None
     vals = []
+    rows = args.ref_rows
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline(x, a, y, b, rows=args.ref_rows)
+        r, rows = cpu_baseline(x, a, y, b, rows=rows, target_s=5.0)  # calibrated once, then fixed
         if k >= args.warmup:
             vals.append(r["value"])
             cb = r
@@ -289,7 +299,7 @@ def main():
     ap.add_argument("--multiscale", type=int, default=1)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-iters", type=int, default=20000)
-    ap.add_argument("--ref-rows", type=int, default=2048)
+    ap.add_argument("--ref-rows", type=int, default=0, help="oracle sample rows (0: about 5-10 s of host work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows-per-thread", type=int, default=0)
     ap.add_argument("--workload", default="density", choices=["density", "fibers", "mlp"])
@@ -433,7 +443,7 @@ def main():
         "wall_s": wall,
     }
     if not args.no_cpu_baseline and world <= 1:
-        line["cpu_baseline"] = cpu_baseline(x, a, y, b)
+        line["cpu_baseline"] = cpu_baseline(x, a, y, b)[0]
     print(json.dumps(line))
     ctx.close()
     if world > 1:
