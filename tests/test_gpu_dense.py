@@ -129,6 +129,28 @@ def test_softmin_far_rows_take_the_safe_path(ctx):
     assert pot_err(got, want, eps) < TOL
 
 
+@pytest.mark.parametrize("D", [3, 60])
+def test_softmin_rows_with_a_wrong_shift_take_the_safe_path(ctx, D):
+    # With old values given, the one-pass kernels shift each row by its old value;
+    # for rows 40 units away from every column an old value of 0 misses the
+    # row's log-sum by far more than 60 binades, so those rows are recomputed by
+    # the two-pass fallback (direct differences).  Every row must equal the
+    # oracle's blended value.
+    from paper_2107_02010_gb300 import otgb
+
+    r = np.random.default_rng(11)
+    q = np.concatenate([r.uniform(0, 1, size=(200, D)), r.uniform(40, 41, size=(56, D))]).astype(np.float32)
+    p = r.uniform(0, 1, size=(300, D)).astype(np.float32)
+    w = r.uniform(0.5, 1.5, size=300).astype(np.float32)
+    w /= w.sum()
+    pot = r.uniform(-0.1, 0.1, size=300).astype(np.float32)
+    old = np.zeros(len(q), np.float32)
+    eps = 0.05
+    got = otgb.softmin(ctx, T(q), T(p), T(w), T(pot), eps, 1.0, old=T(old), omega=0.5)
+    want = 0.5 * oracle.softmin(q, p, w, pot.astype(np.float64), eps, 1.0)
+    assert pot_err(got, want, eps) < TOL
+
+
 # -------------------------------------------------------- dense solve ---
 def _run_pair(ctx, x, a, y, b, blur, reach, q, extra, precision=0):
     from paper_2107_02010_gb300 import otgb
