@@ -145,7 +145,7 @@ def cpu_baseline(x, a, y, b, rows=0, target_s=10.0):
         rows = int(min(x.shape[0], max(2048, 2048 * target_s / max(dt0, 1e-6))))
     dt = run(rows)
     pairs = rows * y.shape[0]
-    return {"value": pairs / dt, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": pairs / dt, "unit": "pairs/s", "cores": oracle.threads(), "kind": "oracle",
             "sample": "FP64 oracle softmin: %d rows x %d columns of the track-density workload (%.1f s)" %
                       (rows, y.shape[0], dt)}, rows
 

@@ -47,6 +47,7 @@ def _load():
         i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
         u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
         ci, cd = C.c_int, C.c_double
+        lib.oracle_threads.argtypes = []; lib.oracle_threads.restype = ci
         lib.oracle_cost.argtypes = [f32p, f32p, ci, ci]; lib.oracle_cost.restype = cd
         lib.oracle_rho.argtypes = [cd, ci]; lib.oracle_rho.restype = cd
         lib.oracle_lambda.argtypes = [cd, cd, ci]; lib.oracle_lambda.restype = cd
@@ -74,6 +75,11 @@ def _load():
         lib.oracle_kmeans.restype = None
         _lib = lib
     return _lib
+
+
+def threads() -> int:
+    """Threads of the oracle's OpenMP row loops (the host cores its timings use)."""
+    return int(_load().oracle_threads())
 
 
 def _f32(a):

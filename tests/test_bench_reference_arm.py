@@ -7,6 +7,8 @@ import os
 import subprocess
 import sys
 
+import oracle
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -22,6 +24,6 @@ def test_reference_arm_prints_one_json_line():
     assert d["metric"] == "softmin pairs/s" and d["unit"] == "pairs/s" and d["higher_is_better"] is True
     assert d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert cb["kind"] == "oracle" and cb["cores"] == oracle.threads() and cb["value"] == d["value"]
     assert "256 rows" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
