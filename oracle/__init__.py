@@ -48,6 +48,8 @@ def _load():
         u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
         ci, cd = C.c_int, C.c_double
         lib.oracle_threads.argtypes = []; lib.oracle_threads.restype = ci
+        lib.oracle_grad_x.argtypes = [f32p, f32p, ci, f32p, f32p, ci, ci, ci, cd, f64p, f64p, f64p, f64p]
+        lib.oracle_grad_x.restype = None
         lib.oracle_cost.argtypes = [f32p, f32p, ci, ci]; lib.oracle_cost.restype = cd
         lib.oracle_rho.argtypes = [cd, ci]; lib.oracle_rho.restype = cd
         lib.oracle_lambda.argtypes = [cd, cd, ci]; lib.oracle_lambda.restype = cd
@@ -154,6 +156,16 @@ def sinkhorn(x, alpha, y, beta, blur, reach=0.0, scaling=0.5, p=2, diameter=0.0,
                                  C.byref(S), info)
     return dict(S=S.value, a=a, b=b, f=f, g=g, iters=int(info[0]), sched_len=int(info[1]), delta=info[2],
                 converged=(rc == 0))
+
+
+def grad_x(x, alpha, y, beta, eps, a, f, g, p=2):
+    """dS/dx (N x D) at the converged duals: a = a^{alpha<->alpha}, f = b^{beta->alpha},
+    g = a^{alpha->beta}.  For dS/dy pass (y, beta, x, alpha, eps, b, g, f)."""
+    x, y = _pts(x), _pts(y)
+    out = np.empty(x.shape, np.float64)
+    _load().oracle_grad_x(x, _f32(alpha), x.shape[0], y, _f32(beta), y.shape[0], x.shape[1], int(p), float(eps),
+                          _f64(a), _f64(f), _f64(g), out)
+    return out
 
 
 def ot_dual(x, alpha, y, beta, eps, rho_, f, g, p=2):

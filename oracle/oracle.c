@@ -428,3 +428,57 @@ void oracle_kmeans(const float *x, const float *w, int N, int D, int K, int iter
     }
     free(acc); free(mass);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the debiased divergence with respect to the points x_i.      */
+/* Section 2 (unbiased Sinkhorn divergences) states that the gradients of S  */
+/* in the weights and the points are expressions of the four dual vectors.  */
+/* Each OT term is a maximum over dual pairs of a function that sees the     */
+/* points only through the cost, so at the optimal duals (envelope theorem)  */
+/*   d OT(alpha, beta) / d x_i   = sum_j pi_ij grad_1 C(x_i, y_j),           */
+/*   d OT(alpha, alpha) / d x_i  = 2 sum_k pi^aa_ik grad_1 C(x_i, x_k)       */
+/* (x_i is in both arguments; C is symmetric), with the plans of Eq. (4):    */
+/* pi_ij = alpha_i beta_j exp((f_i + g_j - C(x_i, y_j)) / eps) and           */
+/* pi^aa_ik = alpha_i alpha_k exp((a_i + a_k - C(x_i, x_k)) / eps).  With    */
+/* S = OT(alpha, beta) - OT(alpha, alpha)/2 - OT(beta, beta)/2 + (mass term, */
+/* free of x):                                                               */
+/*   dS/dx_i = sum_j pi_ij grad_1 C(x_i, y_j) - sum_k pi^aa_ik grad_1 C(x_i, x_k), */
+/* grad_1 C(u, v) = |u - v|^(p-2) (u - v) for C = |u - v|^p / p.  The        */
+/* gradient in y is the same expression with the roles of the two measures   */
+/* exchanged (y, beta, g, b against x, alpha, f).                             */
+/* ------------------------------------------------------------------------ */
+static void add_grad_cost(const float *u, const float *v, int D, int p, double w, double *out)
+{
+    double s = 0.0;
+    for (int d = 0; d < D; ++d) {
+        double t = (double)u[d] - (double)v[d];
+        s += t * t;
+    }
+    double scale = w;
+    if (p != 2) {
+        if (s == 0.0) return;
+        scale *= pow(sqrt(s), (double)p - 2.0);
+    }
+    for (int d = 0; d < D; ++d) out[d] += scale * ((double)u[d] - (double)v[d]);
+}
+
+void oracle_grad_x(const float *x, const float *alpha, int N, const float *y, const float *beta, int M, int D,
+                   int p, double eps, const double *a, const double *f, const double *g, double *grad)
+{
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < N; ++i) {
+        double *gi = grad + (size_t)i * D;
+        for (int d = 0; d < D; ++d) gi[d] = 0.0;
+        const float *xi = x + (size_t)i * D;
+        for (int j = 0; j < M; ++j) {
+            const float *yj = y + (size_t)j * D;
+            double pij = (double)alpha[i] * (double)beta[j] * exp((f[i] + g[j] - cost(xi, yj, D, p)) / eps);
+            add_grad_cost(xi, yj, D, p, pij, gi);
+        }
+        for (int k = 0; k < N; ++k) {
+            const float *xk = x + (size_t)k * D;
+            double pik = (double)alpha[i] * (double)alpha[k] * exp((a[i] + a[k] - cost(xi, xk, D, p)) / eps);
+            add_grad_cost(xi, xk, D, p, -pik, gi);
+        }
+    }
+}
