@@ -118,6 +118,12 @@ typedef struct {
                                 the plain solve (the other fields then describe the plain solve); 0 otherwise */
     int warm_iters;          /* steps spent in the warm attempt */
     double warm_ms;          /* device time of the warm attempt and the network's inference */
+    /* device time of the phases of the solve (CUDA events; they add up to total_ms): */
+    double prep_ms;          /* validation, bounding box, clustering (grid or k-means), reordering and packing */
+    double coarse_ms;        /* coarse solve on the cluster measures and the extrapolation softmin */
+    double fine_ms;          /* full-resolution steps: truncation masks, softmin sweeps, translation,
+                                Anderson mixing and the convergence checks */
+    double final_ms;         /* final FP64 sums of Eq. (6), outputs in the caller's order, finiteness checks */
 } otgb_stats;
 
 /* Fill *p with defaults: p = 2, blur = 0.05, reach = 0 (balanced), scaling = 0.5,
@@ -237,12 +243,12 @@ int otgb_softmin(otgb_ctx *ctx, const float *q, int n_out, const float *p, const
  *   caller, as in otgb_softmin (same arguments, same result).
  *   cuda_stream: the cudaStream_t to run on (NULL: the legacy default stream).
  *   The call returns when the result is complete on that stream.
- * Limits and errors: EINVAL when the scratch of the problem -- about
- * 16 (n_out + n_in) bytes plus 16 bytes per row for D <= 3, and
- * 4 round_up(D, 4) (n_out + n_in) + 4 n_in + 16 n_out bytes for D > 3 --
- * exceeds 16 MiB (for D <= 3 roughly n_out + n_in <= 500,000 when balanced),
- * and for the argument errors of otgb_softmin; the message is available from
- * otgb_last_error(NULL).
+ * Limits and errors: EINVAL when the scratch of the problem exceeds 16 MiB --
+ * about 32 n_out + 16 n_in bytes for D <= 3 (at most about 349,000 rows and
+ * 349,000 columns when n_out = n_in), and
+ * 4 round_up(D, 4) (n_out + n_in) + 4 n_in + 16 n_out bytes for D > 3, plus
+ * about 34 KB in both cases -- and for the argument errors of otgb_softmin;
+ * the message is available from otgb_last_error(NULL).
  * The first call on a device looks up the device address of the scratch
  * array (cudaGetSymbolAddress, with that device current); make that first
  * call before any stream capture.  Every call on a device shares the one

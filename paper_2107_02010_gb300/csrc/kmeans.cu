@@ -177,12 +177,12 @@ std::vector<int> sample_distinct(int n, int K, unsigned long long seed) {
 
 void kmeans_assign(const float *x, int n, int D, const float *cent, int K, int *labels, cudaStream_t st) {
     const int D4 = (D + 3) & ~3;
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice<int> attr;
+    attr.get([] {
         OTGB_CUDA_TRY(cudaFuncSetAttribute(kmeans_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sizeof(AssignSmem)));
-        attr = true;
-    }
+        return 1;
+    });
     kmeans_assign_kernel<<<(n + kAR - 1) / kAR, kAT, sizeof(AssignSmem), st>>>(x, n, D, D4, cent, K, labels);
     OTGB_CHECK_LAUNCH();
 }

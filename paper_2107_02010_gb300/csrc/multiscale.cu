@@ -442,6 +442,7 @@ int Multiscale::run_schedule(Solver &s, const otgb_params &P, const std::vector<
         softmin_run(E, D, s.rows_per_thread, st);
         OTGB_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    OTGB_CUDA_TRY(cudaEventRecord(ctx_event(s.ctx, 3), st));  // end of the coarse phase
     // fine phase over the rest of the schedule
     for (; k < sched.size() && s.steps < P.max_iters; ++k) s.fine_step(sched[k]);
     return OTGB_OK;

@@ -15,7 +15,6 @@ namespace {
 constexpr size_t kNoAllocBytes = 16u << 20;  // 16 MiB, held by every device that loads the library
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[kMaxDevices] = {nullptr};
 
@@ -44,14 +43,16 @@ __global__ void dense_items_kernel(int4 *items, int nb, int n_in) {
     if (k < nb) items[k] = make_int4(0, k, 0, n_in);
 }
 
-// Bump allocator over the scratch array (256-byte aligned pieces).
+// Bump allocator over the scratch array (256-byte aligned pieces).  With a
+// null base it only adds up the sizes (no pointer is formed), which decides
+// whether a problem fits before anything is launched.
 struct Carve {
     unsigned char *base;
     size_t used = 0;
     template <class T> T *take(size_t count) {
-        T *p = reinterpret_cast<T *>(base + used);
+        const size_t off = used;
         used += (count * sizeof(T) + 255) & ~size_t(255);
-        return p;
+        return base ? reinterpret_cast<T *>(base + off) : nullptr;
     }
 };
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <cstdio>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -67,6 +68,30 @@ unsigned long long launch_count();
 inline void require(bool ok, const std::string &msg, int code = OTGB_EINVAL) {
     if (!ok) throw Error{code, msg};
 }
+
+// ------------------------------------------------------------ per device ---
+// Kernel function attributes (the large shared-memory opt-in) and occupancy
+// figures belong to a device, not to the process: a value computed once is
+// cached per device ordinal, and made again, with that device current, the
+// first time each device asks for it.  The lock makes concurrent first calls
+// from several host threads safe.
+constexpr int kMaxDevices = 64;
+int current_device();
+template <class T> struct PerDevice {
+    std::mutex mu;
+    bool set[kMaxDevices] = {};
+    T val[kMaxDevices] = {};
+    template <class F> T get(F &&make) {
+        const int d = current_device();
+        require(d >= 0 && d < kMaxDevices, "device ordinal out of range");
+        std::lock_guard<std::mutex> lock(mu);
+        if (!set[d]) {
+            val[d] = make();
+            set[d] = true;
+        }
+        return val[d];
+    }
+};
 
 // ------------------------------------------------------------- workspace ---
 // Stream-ordered scratch owned by a context.  Buffers are named so that a

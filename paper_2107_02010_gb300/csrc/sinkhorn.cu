@@ -584,13 +584,18 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
             sched.swap(t);
         }
         int rc = OTGB_OK;
+        // phase boundaries: 2 = points prepared (validated, clustered, packed),
+        // 3 = coarse phase and extrapolation done, 4 = iterations done
+        OTGB_CUDA_TRY(cudaEventRecord(ctx_event(ctx, 2), st));
         if (msp) {
             rc = msp->run_schedule(s, P, sched, block_rows);
         } else {
+            OTGB_CUDA_TRY(cudaEventRecord(ctx_event(ctx, 3), st));
             s.setup_dense_instances(block_rows);
             for (size_t k = 0; k < sched.size() && s.steps < P.max_iters; ++k) s.fine_step(sched[k]);
         }
         if (rc == OTGB_OK) rc = s.iterate_at_blur(P, P.max_iters);
+        OTGB_CUDA_TRY(cudaEventRecord(ctx_event(ctx, 4), st));
         if (rc == OTGB_OK || rc == OTGB_ENOCONV) s.S = s.divergence(P.blur * P.blur);
 
         // outputs in the caller's order
@@ -642,6 +647,15 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
             float tot = 0.f;
             OTGB_CUDA_TRY(cudaEventElapsedTime(&tot, ctx_event(ctx, 0), ctx_event(ctx, 1)));
             stats->total_ms = tot;
+            auto span = [&](int a, int b) {
+                float ms = 0.f;
+                OTGB_CUDA_TRY(cudaEventElapsedTime(&ms, ctx_event(ctx, a), ctx_event(ctx, b)));
+                return (double)ms;
+            };
+            stats->prep_ms = span(0, 2);
+            stats->coarse_ms = span(2, 3);
+            stats->fine_ms = span(3, 4);
+            stats->final_ms = span(4, 1);
             stats->last_delta = s.last_delta;
             stats->last_rel_change = s.last_rel;
             stats->fallback_rows = (long long)fbt;

@@ -910,14 +910,14 @@ template <int R, bool TWO>
 void launch_softmin3(const SoftminLaunch &L, cudaStream_t st) {
     int grid = (L.n_items + kW3 - 1) / kW3;
     if (L.work_counter) {
-        static int cap = 0;
-        if (!cap) {
+        static PerDevice<int> cap_of;
+        const int cap = cap_of.get([] {
             int dev = 0, sms = 0, occ = 0;
             OTGB_CUDA_TRY(cudaGetDevice(&dev));
             OTGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
             OTGB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, softmin3_kernel<R, TWO>, 32 * kW3, 0));
-            cap = sms * (occ > 0 ? occ : 1);
-        }
+            return sms * (occ > 0 ? occ : 1);
+        });
         grid = grid < cap ? grid : cap;
     }
     softmin3_kernel<R, TWO><<<grid, 32 * kW3, 0, st>>>(L);
@@ -927,14 +927,13 @@ void launch_softmin3(const SoftminLaunch &L, cudaStream_t st) {
 
 namespace {
 int fallback_grid_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+    static PerDevice<int> sms_of;
+    return sms_of.get([] {
+        int dev = 0, sms = 0;
         OTGB_CUDA_TRY(cudaGetDevice(&dev));
         OTGB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
+        return sms > 0 ? sms : 1;
+    });
 }
 }  // namespace
 
@@ -972,15 +971,15 @@ void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_
         }
     } else {
         const int D4 = (D + 3) & ~3;
-        static bool attr = false;
-        if (!attr) {
+        static PerDevice<int> attr;
+        attr.get([] {
             const int bytes = (int)sizeof(GenSmem);
             OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
             OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<false, 30>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
             OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
             OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_gen_kernel<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-            attr = true;
-        }
+            return 1;
+        });
         if (two) {
             softmin_gen_kernel<true, 0><<<L.n_items, kNTg, sizeof(GenSmem), st>>>(L, D, D4);
             OTGB_CHECK_LAUNCH();

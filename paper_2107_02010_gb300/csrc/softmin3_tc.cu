@@ -402,12 +402,12 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
 }  // namespace
 
 void softmin3_tc_launch(const SoftminLaunch &L, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice<int> attr;
+    attr.get([] {
         OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sizeof(Tc3Smem)));
-        attr = true;
-    }
+        return 1;
+    });
     softmin3_tc_kernel<<<L.n_items, kThreads, sizeof(Tc3Smem), st>>>(L);
     OTGB_CHECK_LAUNCH();
 }

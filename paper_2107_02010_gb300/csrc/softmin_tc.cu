@@ -412,14 +412,14 @@ size_t softmin_tc_smem_bytes() { return sizeof(TcSmem); }
 
 void softmin_tc_launch(const SoftminLaunch &L, int D, cudaStream_t st) {
     const int D4 = (D + 3) & ~3;
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice<int> attr;
+    attr.get([] {
         OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)softmin_tc_smem_bytes()));
         OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)softmin_tc_smem_bytes()));
-        attr = true;
-    }
+        return 1;
+    });
     if (D4 <= 60) softmin_tc_kernel<true><<<L.n_items, 128, softmin_tc_smem_bytes(), st>>>(L, D4);
     else softmin_tc_kernel<false><<<L.n_items, 128, softmin_tc_smem_bytes(), st>>>(L, D4);
     OTGB_CHECK_LAUNCH();

@@ -443,12 +443,12 @@ void tcc_update(const SoftminLaunch &L, cudaStream_t st) {
 void softmin_tcc_launch(const SoftminLaunch &L, int D, cudaStream_t st) {
     const int D4 = (D + 3) & ~3;
     require(D4 <= 60 && L.tcc_nwords <= kMaxWords, "softmin_tcc_launch: unsupported shape", OTGB_EINTERNAL);
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice<int> attr;
+    attr.get([] {
         OTGB_CUDA_TRY(cudaFuncSetAttribute(softmin_tcc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sizeof(TccSmem)));
-        attr = true;
-    }
+        return 1;
+    });
     softmin_tcc_kernel<<<L.n_items, kM, sizeof(TccSmem), st>>>(L, D4);
     OTGB_CHECK_LAUNCH();
 }

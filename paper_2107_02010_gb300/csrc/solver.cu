@@ -17,7 +17,7 @@ struct otgb_ctx {
     cudaStream_t stream = nullptr;
     Workspace ws;
     std::string err;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // pinned host mailbox for small device->host reads
     void *pinned = nullptr;
 };
@@ -36,6 +36,11 @@ bool debug_sync_enabled() {
 }
 void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
 unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+int current_device() {
+    int d = 0;
+    OTGB_CUDA_TRY(cudaGetDevice(&d));
+    return d;
+}
 }  // namespace otgb
 
 namespace otgb {

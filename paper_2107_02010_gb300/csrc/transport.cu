@@ -448,12 +448,12 @@ extern "C" int transport_apply(otgb_ctx *ctx, const otgb_plan *plan, const float
             pack_points(plan->x, nullptr, kr.perm, N, D, d_cen, Rw, nullptr, nullptr, st);
             permute(f, kr.perm, N, fs, st);
             A.rows = Rw; A.f = fs;
-            static bool attr = false;
-            if (!attr) {
+            static PerDevice<int> attr;
+            attr.get([] {
                 OTGB_CUDA_TRY(cudaFuncSetAttribute(transport_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)sizeof(TransportGenSmem)));
-                attr = true;
-            }
+                return 1;
+            });
             transport_gen_kernel<<<(int)hb.size() - 1, kTG, sizeof(TransportGenSmem), st>>>(A, d_blk, lab_off, stride);
             OTGB_CHECK_LAUNCH();
             OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // hb, off released

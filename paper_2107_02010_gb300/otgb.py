@@ -73,6 +73,10 @@ class Stats(C.Structure):
         ("warm_start", C.c_int),
         ("warm_iters", C.c_int),
         ("warm_ms", C.c_double),
+        ("prep_ms", C.c_double),
+        ("coarse_ms", C.c_double),
+        ("fine_ms", C.c_double),
+        ("final_ms", C.c_double),
     ]
 
     def as_dict(self):
@@ -296,10 +300,37 @@ def cluster_kmeans(ctx: Context, x, K, iters=10, seed=0, w=None, init=None):
     return labels, cent, perm, offsets
 
 
-def softmin(ctx: Context, q, p, w, pot, eps, lam=1.0, old=None, omega=0.5):
+def _check_softmin_args(q, p, w, pot, old, out):
+    """Shapes, dtypes and devices of a softmin call, checked before any pointer
+    reaches the library (the kernels trust the sizes they are given)."""
+    if q.dim() != 2 or p.dim() != 2:
+        raise ValueError("q and p must be 2-D (rows x D, columns x D)")
     n_out, D = q.shape
+    n_in = p.shape[0]
+    if p.shape[1] != D:
+        raise ValueError("p has %d coordinates, q has %d" % (p.shape[1], D))
+    if w.numel() != n_in or pot.numel() != n_in:
+        raise ValueError("w and pot must have one entry per column of p (%d)" % n_in)
+    if old is not None and old.numel() != n_out:
+        raise ValueError("old must have one entry per row of q (%d)" % n_out)
+    if out is not None and out.numel() != n_out:
+        raise ValueError("out must have one entry per row of q (%d)" % n_out)
+    for name, t in (("q", q), ("p", p), ("w", w), ("pot", pot), ("old", old), ("out", out)):
+        if t is None:
+            continue
+        if t.dtype != torch.float32:
+            raise ValueError("%s must be float32, got %s" % (name, t.dtype))
+        if t.device != q.device:
+            raise ValueError("%s is on %s, q on %s: all tensors must be on one device" % (name, t.device, q.device))
+    if not q.is_cuda:
+        raise ValueError("expected CUDA tensors")
+    return n_out, n_in, D
+
+
+def softmin(ctx: Context, q, p, w, pot, eps, lam=1.0, old=None, omega=0.5):
+    n_out, n_in, D = _check_softmin_args(q, p, w, pot, old, None)
     out = torch.empty(n_out, device=q.device, dtype=torch.float32)
-    ctx.check(load().otgb_softmin(ctx.h, _f32(q), n_out, _f32(p), _f32(w), _f32(pot), p.shape[0], D, float(eps),
+    ctx.check(load().otgb_softmin(ctx.h, _f32(q), n_out, _f32(p), _f32(w), _f32(pot), n_in, D, float(eps),
                                   float(lam), _f32(old) if old is not None else None, float(omega), _ptr(out)))
     return out
 
@@ -307,15 +338,18 @@ def softmin(ctx: Context, q, p, w, pot, eps, lam=1.0, old=None, omega=0.5):
 def softmin_noalloc(q, p, w, pot, eps, lam=1.0, old=None, omega=0.5, out=None, stream=None):
     """otgb_softmin_noalloc: no context, no device allocation inside the call.
     `out` may be passed preallocated (float32, n_out) so that nothing at all
-    is allocated on the device during the call."""
-    n_out, D = q.shape
-    if out is None:
-        out = torch.empty(n_out, device=q.device, dtype=torch.float32)
-    st = torch.cuda.current_stream(q.device) if stream is None else stream
+    is allocated on the device during the call.  The call runs with q's
+    device current (the library looks up its fixed scratch array on the
+    current device)."""
+    n_out, n_in, D = _check_softmin_args(q, p, w, pot, old, out)
     lib = load()
-    rc = lib.otgb_softmin_noalloc(_f32(q), n_out, _f32(p), _f32(w), _f32(pot), p.shape[0], D, float(eps),
-                                  float(lam), _f32(old) if old is not None else None, float(omega), _ptr(out),
-                                  C.c_void_p(st.cuda_stream))
+    with torch.cuda.device(q.device):
+        if out is None:
+            out = torch.empty(n_out, device=q.device, dtype=torch.float32)
+        st = torch.cuda.current_stream(q.device) if stream is None else stream
+        rc = lib.otgb_softmin_noalloc(_f32(q), n_out, _f32(p), _f32(w), _f32(pot), n_in, D, float(eps),
+                                      float(lam), _f32(old) if old is not None else None, float(omega), _ptr(out),
+                                      C.c_void_p(st.cuda_stream))
     if rc != 0:
         raise OtgbError(rc, lib.otgb_last_error(None).decode())
     return out

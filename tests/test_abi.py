@@ -46,3 +46,34 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(otgb, "_lib", None)
     with pytest.raises(RuntimeError):
         otgb.load(build_if_missing=False)
+
+
+def test_softmin_bindings_reject_mismatched_arguments_before_the_call():
+    # the kernels trust the sizes they are given: a short output or a column
+    # array that does not match would read or write past device buffers, so
+    # the binding refuses such calls before any pointer reaches the library
+    import torch
+
+    from paper_2107_02010_gb300 import otgb
+
+    q, p = torch.zeros(10, 3), torch.zeros(7, 3)
+    w, pot = torch.ones(7), torch.zeros(7)
+    bad = [
+        dict(p=torch.zeros(7, 4)),                       # coordinates differ
+        dict(w=torch.ones(6)),                           # weights of another length
+        dict(pot=torch.zeros(8)),                        # potential of another length
+        dict(out=torch.empty(9)),                        # output too short
+        dict(old=torch.zeros(11)),                       # old of another length
+        dict(w=torch.ones(7, dtype=torch.float64)),      # wrong dtype
+        dict(out=torch.empty(10, dtype=torch.int32)),    # wrong output dtype
+        dict(),                                          # consistent, but on the CPU
+    ]
+    for kw in bad:
+        args = dict(q=q, p=p, w=w, pot=pot, old=None, out=None)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            otgb.softmin_noalloc(args["q"], args["p"], args["w"], args["pot"], 0.1, old=args["old"],
+                                 out=args["out"])
+        if "out" not in kw:
+            with pytest.raises(ValueError):
+                otgb.softmin(None, args["q"], args["p"], args["w"], args["pot"], 0.1, old=args["old"])

@@ -50,6 +50,38 @@ def test_schedule_endpoints_and_length():
     assert len(oracle.schedule(111.0, 1.0, 0.9)) == math.ceil(math.log(111) / math.log(1 / 0.9)) + 1
 
 
+def test_diameter_is_the_joint_bounding_box_diagonal():
+    # Algorithm (Section 2): the schedule starts at a diameter d >= max |x_i - y_j|;
+    # the documented reading is the diagonal of the bounding box of x and y
+    # together.  Here x spans the first axis only and y the second and third,
+    # so the box of x alone, the box of y alone, a missing square root or a
+    # missing axis all give another number than sqrt(1 + 4 + 9).
+    x = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]], np.float32)
+    y = np.array([[0.0, 2.0, 0.0], [0.0, 0.0, -3.0]], np.float32)
+    assert oracle.diameter(x, y) == pytest.approx(math.sqrt(14.0), rel=1e-15)
+    assert oracle.diameter(y, x) == pytest.approx(math.sqrt(14.0), rel=1e-15)
+    # one point: no extent
+    assert oracle.diameter(x[:1], x[:1]) == 0.0
+
+
+@pytest.mark.parametrize("D", [1, 3, 7])
+def test_diameter_bounds_every_pair_distance(D):
+    # an upper bound of the paper's max_ij |x_i - y_j|, and equal to the largest
+    # distance between corners of the joint box (brute force over the corners)
+    r = np.random.default_rng(40 + D)
+    x = r.normal(0.0, 2.0, size=(50, D)).astype(np.float32)
+    y = (r.normal(0.0, 1.0, size=(40, D)) + 3.0).astype(np.float32)
+    d = oracle.diameter(x, y)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    pair_max = np.sqrt(((xd[:, None, :] - yd[None, :, :]) ** 2).sum(-1)).max()
+    assert d >= pair_max
+    both = np.concatenate([xd, yd])
+    lo, hi = both.min(0), both.max(0)
+    corners = np.array(list(itertools.product(*zip(lo, hi))))
+    corner_max = np.sqrt(((corners[:, None, :] - corners[None, :, :]) ** 2).sum(-1)).max()
+    assert d == pytest.approx(corner_max, rel=1e-14)
+
+
 def test_damping_and_rho():
     # lambda = 1/(1+(sigma/reach)^p), rho = reach^p; reach = inf -> balanced.
     assert oracle.lam(1.0, 10.0) == pytest.approx(1.0 / 1.01, rel=1e-15)

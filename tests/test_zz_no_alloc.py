@@ -10,6 +10,8 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
+
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
@@ -39,6 +41,13 @@ def test_noalloc_matches_softmin_two_calls_in_a_row():
         g, h = got.cpu().numpy().astype(np.float64), want.cpu().numpy().astype(np.float64)
         err = np.max(np.abs(g - h)) / (np.max(np.abs(h)) + eps)
         assert err < TOL, (seed, err)
+        # and directly against the FP64 oracle's softmin, blended as the call blends
+        o = old.cpu().numpy().astype(np.float64)
+        tilde = oracle.softmin(q.cpu().numpy(), p.cpu().numpy(), w.cpu().numpy(),
+                               pot.cpu().numpy().astype(np.float64), eps, lam)
+        ref = o + 0.5 * (tilde - o)
+        err = np.max(np.abs(g - ref)) / (np.max(np.abs(ref)) + eps)
+        assert err < TOL, (seed, "oracle", err)
     ctx.close()
 
 
