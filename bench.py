@@ -1,19 +1,25 @@
-"""Benchmark: one step = one full debiased Sinkhorn solve (sinkhorn_divergence)
-on the synthetic track-density workload (two 64^3 density volumes, ~100k
-weighted voxels each, masses 1.0 vs 1.2, p = 2, blur = 1 voxel, reach = 10
-voxels, eps-scaling q = 0.5, multiscale with 4-voxel grid cells), run to the
-stopping rule (estimated remaining relative change of S below 1e-6).
+"""Benchmark of the multiscale debiased Sinkhorn solver on one GB300.
 
-Prints ONE JSON line.  `value` is softmin pairs evaluated per second of solve
-time (all four symmetric instances, whole solve: clustering, coarse phase,
-extrapolation, truncation, fine steps, final FP64 sums).
+Default line -- the scale workload: 60-D fiber bundles, N = M = 1,000,000
+fibers of 20 points per side (20 bundles, features scaled by 1/sqrt(20)),
+coarse-to-fine with k-means of 1000 clusters per side, coarse-plan truncation,
+eps annealed by q = 0.5 per step (on sigma) down to blur = 2 mm, reach = 20 mm,
+FP64 final sums.  One step = one solve of sinkhorn_divergence to its stopping
+rule (estimated remaining relative change of S below 1e-6).
+
+`value` is softmin pairs evaluated per second of solve time of the plain
+float32 form (CUDA cores; all four symmetric instances, whole solve:
+clustering, coarse phase, extrapolation, truncation, fine steps, final sums);
+`time_to_solve_ms` its solve time.  The same line carries the tensor-core form
+(BF16 hi/lo cross term, FP32 accumulation and log-sum-exp) timed the same way,
+and the relative difference of both S from a tightly converged float32 S*.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Other workloads (not the default line; each prints its own JSON line):
-    --workload fibers [--n N] [--precision fp32|tc]   60-D fiber bundles, k-means multiscale,
-        blur 2 mm, reach 20 mm (FP32 or the BF16 hi/lo tensor-core cross term)
-    --workload mlp [--n N]    warm-start network: inference and training throughput
+    --workload fibers --n N       the same fiber problem at N = M = n
+    --workload density            track-density maps (two 64^3 volumes, ~100k voxels, D = 3, grid clusters)
+    --workload mlp [--n N]        warm-start network: inference and training throughput
 """
 from __future__ import annotations
 
@@ -31,54 +37,70 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# Measured per-SM, per-clock rates on GB300 (sm_103a): ex2.approx 32/clk (the
-# MUFU unit), FP32 FMA 128 lanes/clk (f32x2 packing halves issue, not FP32 work).
-# A pair of a stable log-sum-exp in the dot-product form costs D FMAs, one add
-# (the row's reference), one add (accumulate) and one ex2 on the CUDA cores; in
-# the tensor-core forms the exponent comes from the tensor core and the CUDA
-# cores keep one ex2 and one add per pair, so the MUFU unit bounds them.
+# Per-SM, per-clock rates on GB300 (sm_103a) used for the ALU bounds: ex2.approx
+# 32/clk (the MUFU unit, measured), FP32 128 lanes/clk (f32x2 packing halves
+# issue slots, not FP32 work).  A pair of a stable log-sum-exp in the
+# dot-product form costs D FMAs, one add (the row's reference), one add
+# (accumulate) and one ex2 on the CUDA cores; in the tensor-core forms the
+# exponent comes from the tensor core and the CUDA cores keep one ex2 and one
+# add per pair.
 SFU_EX2_PER_CLK_SM = 32
 FP32_LANES_PER_CLK_SM = 128
-# D <= 3, default precision: tensor-core dot product of K = 32 BF16 slots per pair
+# tensor flops per pair: D <= 3 float32-accuracy form (K = 32 BF16 slots), and
+# the 60-D BF16 hi/lo cross term (three K = 64 products)
 TC3_TENSOR_FLOP_PER_PAIR = 2 * 32
-# DRAM bytes (read + write) of one fine-step launch of softmin3_tc_kernel on this
-# workload, from one ncu capture (profiles/softmin3_tc_trackdensity_100k_multiscale.md);
-# to be re-measured whenever that kernel changes
-SOFTMIN3_TC_DRAM_BYTES = 172.6e6
+TC60_TENSOR_FLOP_PER_PAIR = 3 * 2 * 64
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel of each workload, from one capture of the current kernel
+# (null when the kernel has changed since); see the profile summaries.
+TRAFFIC = {
+    "softmin3_tc_kernel": None,
+    "softmin_gen_kernel": None,
+}
 
 
-def workload(args):
-    from paper_2107_02010_gb300 import synth
-
-    x, a, y, b = synth.density_maps(grid=args.grid, n_keep=args.n_keep)
-    return x, a, y, b
+def peaks():
+    return json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
 
 
-def fiber_workload(args):
+def fp32_form_peak(D, clock_mhz, n_sm):
+    per_clk = min(SFU_EX2_PER_CLK_SM, FP32_LANES_PER_CLK_SM / (D + 2))
+    return per_clk * n_sm * clock_mhz * 1e6
+
+
+# ------------------------------------------------------------------ inputs --
+def fiber_data(n):
     from paper_2107_02010_gb300 import synth
 
     ctrl = synth.bundle_centrelines()
-    x, a, _ = synth.fiber_bundles(args.n, seed=4, ctrl=ctrl, perturb=3.0)
-    y, b, _ = synth.fiber_bundles(args.n, seed=5, ctrl=ctrl)
+    x, a, _ = synth.fiber_bundles(n, seed=4, ctrl=ctrl, perturb=3.0)
+    y, b, lab = synth.fiber_bundles(n, seed=5, ctrl=ctrl)
     return x, a, y, b
 
 
-def fiber_params(args, otgb):
+def fiber_params(otgb, n, precision, tol, max_iters):
     return otgb.default_params(blur=2.0, reach=20.0, scaling=0.5, multiscale=1, cluster=1,
-                               k_clusters=max(20, args.n // 1000), kmeans_iters=10, tol=args.tol,
-                               max_iters=args.max_iters, precision=1 if args.precision == "tc" else 0)
+                               k_clusters=max(20, n // 1000), kmeans_iters=10, tol=tol, max_iters=max_iters,
+                               precision=precision)
 
 
-def params_for(args, otgb):
+def density_data(args):
+    from paper_2107_02010_gb300 import synth
+
+    return synth.density_maps(grid=args.grid, n_keep=args.n_keep)
+
+
+def density_params(args, otgb):
     return otgb.default_params(blur=1.0, reach=10.0, scaling=0.5, multiscale=int(args.multiscale), cluster=0,
                                cell=4.0, tol=args.tol, max_iters=args.max_iters, check_every=10,
                                rows_per_thread=args.rows_per_thread)
 
 
+# ------------------------------------------------------------------ clocks --
 def start_clock_sampler():
     try:
         # the raw samples go to the file named by OTGB_CLOCKS_CSV, if set
-        f = open(os.environ.get("OTGB_CLOCKS_CSV") or os.devnull, "w")
+        f = open(os.environ.get("OTGB_CLOCKS_CSV") or os.devnull, "a")
         p = subprocess.Popen(
             ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -124,37 +146,332 @@ def flush_l2(buf):
     buf.add_(1.0)  # touches 256 MB (> 129 MB L2)
 
 
-def cpu_baseline(x, a, y, b, rows=0, target_s=10.0):
-    """The FP64 oracle's softmin on a bounded sample: `rows` rows of the
-    alpha->beta instance against all columns, at eps = blur^2.  rows = 0: a
-    calibration run of 2048 rows sets the row count for about target_s seconds
-    (at most every row).  Returns (the cpu_baseline object, rows used)."""
+# ------------------------------------------------------------ CPU baseline --
+def oracle_rows_timing(x, y, b, eps, lam, rows, threads=0):
+    """Seconds the FP64 oracle takes for the softmin of `rows` rows of x (evenly
+    spread) against all columns y (pot = 0), on `threads` threads (0: all)."""
     import oracle
 
     oracle.build()
+    if threads:
+        oracle.set_threads(threads)
     pot = np.zeros(y.shape[0])
+    idx = np.linspace(0, x.shape[0] - 1, rows).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.softmin(x[idx], y, b, pot, eps, lam)
+    return time.perf_counter() - t0
 
-    def run(n):
-        idx = np.linspace(0, x.shape[0] - 1, n).astype(np.int64)
-        t0 = time.perf_counter()
-        oracle.softmin(x[idx], y, b, pot, 1.0, 1.0 / 1.01)
-        return time.perf_counter() - t0
 
+def oracle_calibrated(x, y, b, eps, lam, target_s, rows=0, probe=64, threads=0):
+    """(rows, seconds): a probe run sets the row count for about target_s."""
     if rows <= 0:
-        dt0 = run(2048)
-        rows = int(min(x.shape[0], max(2048, 2048 * target_s / max(dt0, 1e-6))))
-    dt = run(rows)
-    pairs = rows * y.shape[0]
-    return {"value": pairs / dt, "unit": "pairs/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": "FP64 oracle softmin: %d rows x %d columns of the track-density workload (%.1f s)" %
-                      (rows, y.shape[0], dt)}, rows
+        dt0 = oracle_rows_timing(x, y, b, eps, lam, probe, threads)
+        rows = int(min(x.shape[0], max(probe, probe * target_s / max(dt0, 1e-6))))
+    return rows, oracle_rows_timing(x, y, b, eps, lam, rows, threads)
 
 
-def peak_pairs_per_s(D, clock_mhz, n_sm):
-    per_clk = min(SFU_EX2_PER_CLK_SM, FP32_LANES_PER_CLK_SM / (D + 2))
-    return per_clk * n_sm * clock_mhz * 1e6
+def cpu_baseline(x, y, b, eps, lam, label, target_s=10.0, one_core_s=4.0, solve_pairs_dense=None, probe=64):
+    """The FP64 oracle's softmin on a bounded sample of the workload, on all the
+    host cores and on one core; with solve_pairs_dense (dense pairs of the
+    solve: steps x (N^2 + M^2 + 2NM)) the oracle's solve time is extrapolated."""
+    import oracle
+
+    oracle.build()
+    cores = oracle.threads()
+    rows, dt = oracle_calibrated(x, y, b, eps, lam, target_s, probe=probe)
+    rate = rows * y.shape[0] / dt
+    r1, dt1 = oracle_calibrated(x, y, b, eps, lam, one_core_s, probe=max(4, probe // 8), threads=1)
+    oracle.set_threads(cores)
+    out = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+           "sample": "FP64 oracle softmin: %d rows x %d columns of the %s (%.1f s on %d threads)" %
+                     (rows, y.shape[0], label, dt, cores),
+           "one_core": {"value": r1 * y.shape[0] / dt1, "unit": "pairs/s", "cores": 1,
+                        "sample": "%d rows x %d columns (%.1f s)" % (r1, y.shape[0], dt1)}}
+    if solve_pairs_dense:
+        out["extrapolated_solve_s"] = solve_pairs_dense / rate
+        out["extrapolated_solve_s_one_core"] = solve_pairs_dense / out["one_core"]["value"]
+        out["extrapolation"] = ("extrapolated, not measured: the GPU solve's steps x dense pairs per step "
+                                "(N^2 + M^2 + 2NM) / the oracle's pairs/s (the oracle evaluates every pair)")
+    return out
 
 
+# ------------------------------------------------------------------ timing --
+def timed_solves(solve, steps, warmup, l2, st):
+    """W untimed solves, then K solves each bracketed by CUDA events on the
+    launching stream, with a 256 MB write between them (L2 flush)."""
+    import torch
+
+    for _ in range(warmup):
+        solve()
+    torch.cuda.synchronize()
+    ms, outs = [], []
+    for _ in range(steps):
+        flush_l2(l2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        out = solve()
+        e1.record(st)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        outs.append(out)
+    torch.cuda.synchronize()
+    return ms, outs
+
+
+def summarize(ms, outs):
+    keys = ("prep_ms", "coarse_ms", "fine_ms", "final_ms")
+    st = [o["stats"] for o in outs]
+    return {
+        "time_to_solve_ms": statistics.mean(ms),
+        "pairs_per_solve": statistics.mean(s["pairs_evaluated"] for s in st),
+        "softmin_ms_per_solve": statistics.mean(s["softmin_ms"] for s in st),
+        "iters_per_solve": statistics.mean(s["iters_total"] for s in st),
+        "S": outs[-1]["S"],
+        "converged": all(o["status"] == 0 for o in outs),
+        "phases_ms": {k[:-3]: statistics.mean(s[k] for s in st) for k in keys},
+        "kept_fraction": st[-1]["kept_fraction"],
+    }
+
+
+def e2e_solves(solve_host, repeats):
+    """End to end through the public API: pinned host inputs copied in, the
+    solve, S and the duals f, g read back; wall time per repeat."""
+    import torch
+
+    solve_host()  # one untimed pass (same buffers as the timed ones)
+    out = []
+    for _ in range(repeats):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        solve_host()
+        torch.cuda.synchronize()
+        out.append((time.perf_counter() - t1) * 1e3)
+    return out
+
+
+def dist_setup():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    import torch
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+
+# ------------------------------------------------------------------ fibers --
+def run_fibers(args):
+    """60-D fibers, N = M = n: the float32 form (the line's value) and the
+    tensor-core form, each W warm-up + K timed solves to the stopping rule."""
+    import torch
+
+    world, rank, local = dist_setup()
+    from paper_2107_02010_gb300 import otgb, replicas
+
+    n = args.n
+    x, a, y, b = fiber_data(n)
+    dev = torch.device("cuda", local)
+    X, A, Y, B = (torch.from_numpy(v).to(dev) for v in (x, a, y, b))
+    ctx = otgb.Context()
+    st = torch.cuda.current_stream(dev)
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    p32 = fiber_params(otgb, n, 0, args.tol, args.max_iters)
+    ptc = fiber_params(otgb, n, 1, args.tol, args.max_iters)
+    solve32 = lambda: otgb.sinkhorn_divergence(ctx, X, A, Y, B, p32, raise_on_noconv=False)
+    solvetc = lambda: otgb.sinkhorn_divergence(ctx, X, A, Y, B, ptc, raise_on_noconv=False)
+    D = x.shape[1]
+    pk = peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = pk.get("sm_max_mhz", 2070.0)
+
+    # float32 form: the line's value
+    barrier(world)
+    sampler, sf = start_clock_sampler()
+    l0 = otgb.kernel_launches()
+    ms32, outs32 = timed_solves(solve32, args.steps, args.warmup, l2, st)
+    launches = otgb.kernel_launches() - l0
+    clocks = stop_clock_sampler(sampler, sf, local)
+    barrier(world)
+    s32 = summarize(ms32, outs32)
+    t_total, pairs = replicas.aggregate(sum(ms32) / 1e3, s32["pairs_per_solve"] * args.steps, dev)
+    value = pairs / t_total
+
+    # tensor-core form
+    tc = None
+    if not args.no_tc:
+        sampler, sf = start_clock_sampler()
+        mstc, outstc = timed_solves(solvetc, args.steps, args.warmup, l2, st)
+        clocks_tc = stop_clock_sampler(sampler, sf, local)
+        tc = summarize(mstc, outstc)
+        tc["clocks"] = clocks_tc
+
+    # S* of the stopping-rule check: one tightly converged float32 solve (untimed)
+    # (at least 60 steps at blur, past the point where the float32 iteration stops contracting)
+    pref = fiber_params(otgb, n, 0, 1e-9, 20000)
+    pref.min_iters = 60
+    ref = otgb.sinkhorn_divergence(ctx, X, A, Y, B, pref, raise_on_noconv=False)
+    S_star = ref["S"]
+
+    # end to end through the public API from pinned host buffers
+    hx, ha, hy, hb = (torch.from_numpy(v).pin_memory() for v in (x, a, y, b))
+
+    def solve_host():
+        Xd, Ad, Yd, Bd = (h.to(dev, non_blocking=True) for h in (hx, ha, hy, hb))
+        o = otgb.sinkhorn_divergence(ctx, Xd, Ad, Yd, Bd, p32, raise_on_noconv=False)
+        o["f"].cpu(), o["g"].cpu()
+        return o
+
+    e2e_ms = e2e_solves(solve_host, max(1, min(args.steps, args.e2e_steps)))
+    e2e_val = s32["pairs_per_solve"] / (statistics.mean(e2e_ms) / 1e3) * max(world, 1)
+    h2d = sum(v.nbytes for v in (x, a, y, b))
+    d2h = 4 * (x.shape[0] + y.shape[0])
+
+    # roofline of the dominant kernel (softmin_gen_kernel: 60-D float32 dot-product form)
+    peak = fp32_form_peak(D, clk, n_sm)
+    achieved = s32["pairs_per_solve"] / (s32["softmin_ms_per_solve"] / 1e3)
+    line = {
+        "metric": "softmin pairs/s", "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": s32["time_to_solve_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "60-D fiber bundles (20 points x 3-D, scaled 1/sqrt(20)), 20 bundles, N=M=%d, "
+                               "k-means %d clusters per side, coarse-plan truncation, blur 2 mm, reach 20 mm, "
+                               "q 0.5, FP64 final sums, stop at est. rel. change of S < %g" %
+                               (n, max(20, n // 1000), args.tol),
+                   "N": n, "M": n, "D": D,
+                   "l2": "inputs larger than L2 (240 MB per side); 256 MB buffer written between timed steps",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "time_to_solve_ms": s32["time_to_solve_ms"],
+        "S": s32["S"], "S_star": S_star, "rel_err_S": abs(s32["S"] - S_star) / abs(S_star),
+        "S_star_from": "float32 solve to est. rel. change < 1e-9, at least 60 steps at blur (%d steps)" %
+                       ref["stats"]["iters_total"],
+        "converged": s32["converged"], "iters_per_solve": s32["iters_per_solve"],
+        "pairs_per_solve": s32["pairs_per_solve"], "kept_fraction": s32["kept_fraction"],
+        "softmin_ms_per_solve": s32["softmin_ms_per_solve"], "phases_ms": s32["phases_ms"],
+        "roofline": {"bound": "alu", "kernel": "softmin_gen_kernel (+ fallback), 60-D float32 dot-product form",
+                     "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpairs/s", "frac": achieved / peak,
+                     "traffic": TRAFFIC["softmin_gen_kernel"],
+                     "peak_basis": "FP32: %d SMs x 128 lanes/clk / (D + 2) FP32 ops per pair x %.0f MHz "
+                                   "(sm_max_mhz of MEASURED_PEAKS.json); MUFU ex2 (32/clk) is not binding at "
+                                   "D = 60" % (n_sm, clk)},
+        "e2e": {"value": e2e_val, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "repeats": len(e2e_ms), "ms_per_step": statistics.mean(e2e_ms)},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    if tc is not None:
+        peak_tc = min(pk.get("bf16_tflops", 1910.7) * 1e12 / TC60_TENSOR_FLOP_PER_PAIR,
+                      SFU_EX2_PER_CLK_SM * n_sm * clk * 1e6)
+        ach_tc = tc["pairs_per_solve"] / (tc["softmin_ms_per_solve"] / 1e3)
+        tc.update({"dtype": "bf16 hi/lo cross term (three products), f32 accumulate, f32 log-sum-exp",
+                   "rel_err_S": abs(tc["S"] - S_star) / abs(S_star),
+                   "speedup_vs_fp32": s32["time_to_solve_ms"] / tc["time_to_solve_ms"],
+                   "value": tc["pairs_per_solve"] / (tc["time_to_solve_ms"] / 1e3),
+                   "roofline": {"bound": "tensor", "kernel": "softmin_tcc_kernel (cluster-tiled tcgen05 form)",
+                                "achieved": ach_tc / 1e9, "peak": peak_tc / 1e9, "unit": "Gpairs/s",
+                                "frac": ach_tc / peak_tc,
+                                "peak_basis": "bf16 burst of measured / %d flop per pair" %
+                                              TC60_TENSOR_FLOP_PER_PAIR}})
+        line["tensor_core_form"] = tc
+    if not args.no_cpu_baseline and world <= 1:
+        dense = (2.0 * n * n + 2.0 * n * n) * s32["iters_per_solve"]
+        line["cpu_baseline"] = cpu_baseline(x, y, b, 4.0, 1.0 / 1.01, "60-D fiber workload", target_s=10.0,
+                                            one_core_s=4.0, solve_pairs_dense=dense, probe=16)
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+# ----------------------------------------------------------------- density --
+def run_density(args):
+    """Track-density maps (D = 3, grid clusters): one solve per step."""
+    import torch
+
+    world, rank, local = dist_setup()
+    from paper_2107_02010_gb300 import otgb, replicas
+
+    x, a, y, b = density_data(args)
+    dev = torch.device("cuda", local)
+    X, A, Y, B = (torch.from_numpy(v).to(dev) for v in (x, a, y, b))
+    ctx = otgb.Context()
+    p = density_params(args, otgb)
+    st = torch.cuda.current_stream(dev)
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    solve = lambda: otgb.sinkhorn_divergence(ctx, X, A, Y, B, p, raise_on_noconv=False)
+    barrier(world)
+    sampler, sf = start_clock_sampler()
+    l0 = otgb.kernel_launches()
+    ms, outs = timed_solves(solve, args.steps, args.warmup, l2, st)
+    launches = otgb.kernel_launches() - l0
+    clocks = stop_clock_sampler(sampler, sf, local)
+    barrier(world)
+    s = summarize(ms, outs)
+    t_total, pairs = replicas.aggregate(sum(ms) / 1e3, s["pairs_per_solve"] * args.steps, dev)
+    hx, ha, hy, hb = (torch.from_numpy(v).pin_memory() for v in (x, a, y, b))
+
+    def solve_host():
+        Xd, Ad, Yd, Bd = (h.to(dev, non_blocking=True) for h in (hx, ha, hy, hb))
+        o = otgb.sinkhorn_divergence(ctx, Xd, Ad, Yd, Bd, p, raise_on_noconv=False)
+        o["f"].cpu(), o["g"].cpu()
+
+    e2e_ms = e2e_solves(solve_host, args.steps)
+    pk = peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = pk.get("sm_max_mhz", 2070.0)
+    # the default D <= 3 kernel (softmin3_tc_kernel): min(MUFU ex2, tensor pipe)
+    peak_mufu = SFU_EX2_PER_CLK_SM * n_sm * clk * 1e6
+    peak_tensor = pk.get("bf16_tflops", 1910.7) * 1e12 / TC3_TENSOR_FLOP_PER_PAIR
+    peak = min(peak_mufu, peak_tensor)
+    achieved = s["pairs_per_solve"] / (s["softmin_ms_per_solve"] / 1e3)
+    line = {
+        "metric": "softmin pairs/s", "workload": "density", "value": pairs / t_total, "unit": "pairs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": s["time_to_solve_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3 three-piece exponent on the tensor cores (float32 accuracy), f32 sums",
+        "data": "synthetic",
+        "config": {"workload": "track-density maps: two 64^3 volumes of 30 Gaussian tubes, %d voxels per side, "
+                               "masses 1.0/1.2, p=2, blur=1, reach=10, q=0.5, multiscale grid cells of 4 voxels, "
+                               "stop at est. rel. change of S < %g" % (x.shape[0], args.tol),
+                   "N": int(x.shape[0]), "M": int(y.shape[0]), "D": 3,
+                   "l2": "256 MB buffer written between timed steps (inputs are smaller than L2)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        **s,
+        "roofline": {"bound": "alu", "kernel": "softmin3_tc_kernel (+ fallback)", "achieved": achieved / 1e9,
+                     "peak": peak / 1e9, "unit": "Gpairs/s", "frac": achieved / peak,
+                     "traffic": TRAFFIC["softmin3_tc_kernel"],
+                     "peak_basis": "MUFU ex2: %d SMs x 32 ex2/clk x %.0f MHz, below the tensor bound %.3g pairs/s "
+                                   "(bf16 of measured, %d flop per pair)" % (n_sm, clk, peak_tensor,
+                                                                            TC3_TENSOR_FLOP_PER_PAIR)},
+        "e2e": {"value": s["pairs_per_solve"] / (statistics.mean(e2e_ms) / 1e3) * max(world, 1), "unit": "pairs/s",
+                "h2d_bytes_per_step": sum(v.nbytes for v in (x, a, y, b)),
+                "d2h_bytes_per_step": 4 * (x.shape[0] + y.shape[0])},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world <= 1:
+        line["cpu_baseline"] = cpu_baseline(x, y, b, 1.0, 1.0 / 1.01, "track-density workload", target_s=10.0,
+                                            one_core_s=4.0, probe=2048)
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+# --------------------------------------------------------------------- mlp --
 def run_mlp(args):
     """Warm-start network throughput: inference over n rows and one training
     epoch over n rows (batches of 16384), FLOPs counted as 2 per multiply-add of
@@ -188,8 +505,7 @@ def run_mlp(args):
     torch.cuda.synchronize()
     inf_ms = ev[0].elapsed_time(ev[1]) / args.steps
     tr_ms = ev[2].elapsed_time(ev[3]) / args.steps
-    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-    peak = peaks.get("bf16_tflops", 1900.0)
+    peak = peaks().get("bf16_tflops", 1910.7)
     line = {"metric": "warm-start network TFLOP/s", "workload": "mlp", "unit": "TFLOP/s",
             "value": fwd / inf_ms / 1e9, "steps": args.steps, "warmup": args.warmup, "dtype": "bf16",
             "data": "synthetic", "higher_is_better": True,
@@ -204,85 +520,38 @@ def run_mlp(args):
     return 0
 
 
-def run_fibers(args):
-    """60-D fiber bundles (N = M = n), k-means multiscale, FP32 or tensor-core
-    form; one step = one solve to the stopping rule."""
-    import torch
-    from paper_2107_02010_gb300 import otgb
-
-    x, a, y, b = fiber_workload(args)
-    X, A, Y, B = (torch.from_numpy(v).cuda() for v in (x, a, y, b))
-    ctx = otgb.Context()
-    p = fiber_params(args, otgb)
-    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        out = otgb.sinkhorn_divergence(ctx, X, A, Y, B, p, raise_on_noconv=False)
-    torch.cuda.synchronize()
-    sampler, sf = start_clock_sampler()
-    st = torch.cuda.current_stream()
-    l0 = otgb.kernel_launches()
-    ms, pairs, smin = [], 0.0, 0.0
-    for _ in range(args.steps):
-        flush_l2(l2)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        out = otgb.sinkhorn_divergence(ctx, X, A, Y, B, p, raise_on_noconv=False)
-        e1.record(st)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        pairs += out["stats"]["pairs_evaluated"]
-        smin += out["stats"]["softmin_ms"]
-    clocks = stop_clock_sampler(sampler, sf)
-    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    clk = peaks.get("sm_max_mhz", 2070.0)
-    D = x.shape[1]
-    if args.precision == "tc":
-        # three K = 64 BF16 MMAs per pair (hi.hi, hi.lo, lo.hi); the MUFU bound is higher
-        peak = min(peaks.get("bf16_tflops", 1929.8) * 1e12 / (3 * 2 * 64), SFU_EX2_PER_CLK_SM * n_sm * clk * 1e6)
-        basis = "tensor: bf16 of measured / 384 flop per pair (MUFU %d SMs x 32/clk is higher)" % n_sm
-        bound = "tensor"
-    else:
-        peak = peak_pairs_per_s(D, clk, n_sm)
-        basis = "FP32 form: %d SMs x min(32, 128/(D+2)) pairs/clk x %.0f MHz" % (n_sm, clk)
-        bound = "alu"
-    achieved = pairs / (smin / 1e3) if smin > 0 else None
-    line = {"metric": "softmin pairs/s", "workload": "fibers", "value": pairs / (sum(ms) / 1e3), "unit": "pairs/s",
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
-            "higher_is_better": True, "dtype": "f32" if args.precision == "fp32" else "bf16x3+f32",
-            "data": "synthetic",
-            "config": {"workload": "fiber bundles 60-D, N=M=%d, k-means %d clusters, blur 2, reach 20, q 0.5, %s" %
-                                   (args.n, max(20, args.n // 1000), args.precision)},
-            "time_to_solve_ms": statistics.mean(ms), "iters_per_solve": out["stats"]["iters_total"],
-            "S": out["S"], "last_stats": out["stats"],
-            "roofline": {"bound": bound, "achieved": achieved / 1e9 if achieved else None, "peak": peak / 1e9,
-                         "unit": "Gpairs/s", "frac": achieved / peak if achieved else None, "peak_basis": basis},
-            "gpu_launches": int(otgb.kernel_launches() - l0), "clocks": clocks}
-    print(json.dumps(line))
-    return 0
-
-
+# --------------------------------------------------------------- reference --
 def run_reference(args):
+    """The reference arm: the FP64 oracle timed on the host cores, each step a
+    bounded sample of the same workload (rows of the beta -> alpha softmin
+    against all columns), calibrated once to about 5 s of host work."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    x, a, y, b = workload(args)
-    cb = None
-    vals = []
+    if args.workload == "density":
+        x, a, y, b = density_data(args)
+        eps, label, probe = 1.0, "track-density maps 64^3, ~%d voxels per side" % x.shape[0], 2048
+    else:
+        x, a, y, b = fiber_data(args.n)
+        eps, label, probe = 4.0, "60-D fiber bundles, N=M=%d" % args.n, 16
+    lam = 1.0 / 1.01
     rows = args.ref_rows
+    vals, last = [], None
     for k in range(args.warmup + args.steps):
-        r, rows = cpu_baseline(x, a, y, b, rows=rows, target_s=5.0)  # calibrated once, then fixed
+        rows, dt = oracle_calibrated(x, y, b, eps, lam, 5.0, rows=rows, probe=probe)
         if k >= args.warmup:
-            vals.append(r["value"])
-            cb = r
+            vals.append(rows * y.shape[0] / dt)
+            last = (rows, dt)
+    import oracle
+
     v = statistics.mean(vals)
     line = {"impl": "reference", "metric": "softmin pairs/s", "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "track-density maps 64^3, ~%d voxels per side, FP64 oracle softmin sample" %
-                                   x.shape[0]},
-            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": cb["cores"], "kind": "oracle",
-                             "sample": cb["sample"]},
+            "config": {"workload": label + ", FP64 oracle softmin sample"},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": "FP64 oracle softmin: %d rows x %d columns per step (%.1f s)" %
+                                       (last[0], y.shape[0], last[1])},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -294,161 +563,30 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fibers", choices=["fibers", "density", "mlp"])
+    ap.add_argument("--n", type=int, default=0, help="fibers: points per side (1,000,000); mlp: rows (1,048,576)")
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--n-keep", type=int, default=100_000)
     ap.add_argument("--multiscale", type=int, default=1)
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--max-iters", type=int, default=20000)
-    ap.add_argument("--ref-rows", type=int, default=0, help="oracle sample rows (0: about 5-10 s of host work)")
+    ap.add_argument("--max-iters", type=int, default=5000)
+    ap.add_argument("--ref-rows", type=int, default=0, help="oracle sample rows (0: calibrated to about 5 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tc", action="store_true", help="fibers: skip the tensor-core form")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="fibers: end-to-end repeats")
     ap.add_argument("--rows-per-thread", type=int, default=0)
-    ap.add_argument("--workload", default="density", choices=["density", "fibers", "mlp"])
-    ap.add_argument("--n", type=int, default=0, help="fibers: points per side (200000); mlp: rows (1048576)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tc"])
     args = ap.parse_args()
+    if args.workload == "fibers":
+        args.n = args.n or 1_000_000
+    elif args.workload == "mlp":
+        args.n = args.n or (1 << 20)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "fibers":
-        args.n = args.n or 200_000
-        args.max_iters = min(args.max_iters, 5000)
-        return run_fibers(args)
+    if args.workload == "density":
+        return run_density(args)
     if args.workload == "mlp":
-        args.n = args.n or (1 << 20)
         return run_mlp(args)
-
-    import torch
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    from paper_2107_02010_gb300 import otgb
-
-    # Independent replicas: every rank solves its own copy of the workload; no
-    # data-path collective exists in the method on one problem.
-    x, a, y, b = workload(args)
-    dev = torch.device("cuda", local)
-    X, A, Y, B = (torch.from_numpy(v).to(dev) for v in (x, a, y, b))
-    ctx = otgb.Context()
-    p = params_for(args, otgb)
-    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-
-    solve = lambda *t: otgb.sinkhorn_divergence(ctx, *t, p, raise_on_noconv=False)
-    for _ in range(args.warmup):
-        out = solve(X, A, Y, B)
-    torch.cuda.synchronize()
-
-    sampler, sf = start_clock_sampler()
-    st = torch.cuda.current_stream()
-    launches0 = otgb.kernel_launches()
-    step_ms, pairs, smin_ms, iters, S_vals, statuses = [], 0.0, 0.0, [], [], []
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush_l2(l2)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        out = solve(X, A, Y, B)
-        e1.record(st)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        s = out["stats"]
-        pairs += s["pairs_evaluated"]
-        smin_ms += s["softmin_ms"]
-        iters.append(s["iters_total"])
-        S_vals.append(out["S"])
-        statuses.append(out["status"])
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    wall = time.perf_counter() - t0
-    launches = otgb.kernel_launches() - launches0
-    clocks = stop_clock_sampler(sampler, sf, local)
-
-    ms_per_step = statistics.mean(step_ms)
-    t_total = sum(step_ms) / 1e3
-    from paper_2107_02010_gb300 import replicas
-
-    t_total, pairs = replicas.aggregate(t_total, pairs, dev)
-    value = pairs / t_total
-
-    # end to end through the public API with host buffers: pinned host inputs
-    # copied in, the solve, and S plus the potentials f, g read back
-    hx, ha, hy, hb = (torch.from_numpy(v).pin_memory() for v in (x, a, y, b))
-    e2e_ms = []
-    for k in range(args.steps + 1):
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        Xd, Ad, Yd, Bd = (h.to(dev, non_blocking=True) for h in (hx, ha, hy, hb))
-        o = solve(Xd, Ad, Yd, Bd)
-        fh, gh = o["f"].cpu(), o["g"].cpu()
-        torch.cuda.synchronize()
-        if k > 0:
-            e2e_ms.append((time.perf_counter() - t1) * 1e3)
-    pairs_per = pairs / args.steps / max(world, 1)
-    e2e_val = pairs_per / (statistics.mean(e2e_ms) / 1e3) * max(world, 1)
-    h2d = sum(v.nbytes for v in (x, a, y, b))
-    d2h = 4 * (x.shape[0] + y.shape[0]) + 8
-
-    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    clk = peaks.get("sm_max_mhz", 2070.0)
-    # the default D <= 3 kernel (softmin3_tc_kernel): min(MUFU ex2, tensor pipe)
-    peak_mufu = SFU_EX2_PER_CLK_SM * n_sm * clk * 1e6
-    peak_tensor = peaks.get("bf16_tflops", 1929.8) * 1e12 / TC3_TENSOR_FLOP_PER_PAIR
-    peak = min(peak_mufu, peak_tensor)
-    peak_fp32_form = peak_pairs_per_s(3, clk, n_sm)
-    achieved = pairs / max(world, 1) / (smin_ms / 1e3) if smin_ms > 0 else None
-
-    if rank != 0:
-        return 0
-    line = {
-        "metric": "softmin pairs/s", "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "track-density maps: two 64^3 volumes of 30 Gaussian tubes, %d voxels per side, "
-                               "masses 1.0/1.2, p=2, blur=1, reach=10, q=0.5, %s, stop at est. rel. change of "
-                               "S < %g" % (x.shape[0], "multiscale grid cells of 4 voxels" if args.multiscale
-                                           else "dense single scale", args.tol),
-                   "N": int(x.shape[0]), "M": int(y.shape[0]), "D": 3,
-                   "l2": "256 MB buffer written between timed steps (inputs are smaller than L2)",
-                   "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "time_to_solve_ms": ms_per_step,
-        "iters_per_solve": statistics.mean(iters),
-        "S": S_vals[-1],
-        "converged": all(v == 0 for v in statuses),
-        "last_stats": out["stats"],
-        "softmin_ms_per_solve": smin_ms / args.steps,
-        "pairs_per_solve": pairs_per,
-        "roofline": {"bound": "alu", "kernel": "softmin3_tc_kernel (+ fallback), per softmin launch",
-                     "achieved": achieved / 1e9 if achieved else None, "peak": peak / 1e9, "unit": "Gpairs/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": SOFTMIN3_TC_DRAM_BYTES,
-                     "traffic_unit": "bytes per fine-step launch (ncu dram__bytes_read + write)",
-                     "peak_basis": "MUFU ex2: %d SMs x 32 ex2/clk x %.0f MHz (measured per-clock rate; clock = "
-                                   "sm_max_mhz of MEASURED_PEAKS.json), below the tensor bound %.3g pairs/s "
-                                   "(bf16, of measured, %d flop per pair)" % (n_sm, clk, peak_tensor,
-                                                                            TC3_TENSOR_FLOP_PER_PAIR),
-                     "fp32_form_peak": peak_fp32_form / 1e9,
-                     "frac_of_fp32_form_peak": (achieved / peak_fp32_form) if achieved else None},
-        "e2e": {"value": e2e_val, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
-        "clocks": clocks,
-        "wall_s": wall,
-    }
-    if not args.no_cpu_baseline and world <= 1:
-        line["cpu_baseline"] = cpu_baseline(x, a, y, b)[0]
-    print(json.dumps(line))
-    ctx.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
-    return 0
+    return run_fibers(args)
 
 
 if __name__ == "__main__":

@@ -95,6 +95,11 @@ typedef struct {
                               of 0.  Default 0. */
     int warm_max_iters;    /* sinkhorn_divergence_warm: step budget of the warm attempt before it falls
                               back to the plain solve; <= 0: max_iters.  Default 0. */
+    int debug_wait_probe;  /* test hook of the bounded-wait error path: 1 = the solve also runs one device
+                              wait on a word that nothing writes; it gives up after about a millisecond,
+                              flags the error word that the tensor-core and tile waits use, and the solve
+                              (whose outputs are still written) returns OTGB_ETIMEOUT.  Nothing faults or
+                              hangs and the context stays usable.  0 = off (default). */
 } otgb_params;
 
 /* Statistics of one solve (host struct, filled when non-null). */
@@ -210,6 +215,47 @@ int cluster_grid(otgb_ctx *ctx, const float *x, const float *w, int N, int D, fl
 int cluster_kmeans(otgb_ctx *ctx, const float *x, const float *w, int N, int D, int K, int iters,
                    unsigned long long seed, const float *init, int32_t *labels, float *centroids, int32_t *perm,
                    int32_t *offsets);
+
+/*
+ * Gradient of the debiased divergence in the points of the first measure
+ * (Section 2, "Unbiased Sinkhorn divergences": at the fixed point the
+ * gradients of S are expressions of the dual vectors).  For the cost
+ * C(x, y) = |x - y|^2 / 2:
+ *   grad_i = alpha_i [ sum_j beta_j  exp((f_i + g_j - C(x_i, y_j)) / eps) (x_i - y_j)
+ *                    - sum_k alpha_k exp((a_i + a_k - C(x_i, x_k)) / eps) (x_i - x_k) ]
+ * = dS_{eps,rho}(alpha, beta) / dx_i, with (f, g) the dual pair of
+ * OT(alpha, beta) and a the symmetric dual of OT(alpha, alpha) that
+ * sinkhorn_divergence wrote (f, g, a_self; caller order) at eps = blur^p.
+ * The gradient in y is the same call with the measures exchanged:
+ * (y, beta, M, x, alpha, N, ..., f := g, g := f, a_self := b_self).
+ *   x: N x D, alpha: N, y: M x D, beta: M, f: N, g: M, a_self: N (device);
+ *   grad: N x D device output (float32).
+ * Dense: every pair is summed (the direct difference form of the cost, FP32,
+ * with a running maximum per row), for any 1 <= D <= 64.
+ * Errors: EINVAL for null pointers, sizes < 1, D outside [1, 64], p != 2, eps <= 0.
+ */
+int sinkhorn_grad_x(otgb_ctx *ctx, const float *x, const float *alpha, int N, const float *y, const float *beta,
+                    int M, int D, int p, double eps, const float *f, const float *g, const float *a_self,
+                    float *grad);
+
+/*
+ * Free-support Wasserstein barycenter (Section 2, "Track density atlas"):
+ * minimises (1/K) sum_k S_{eps,rho}(alpha, beta_k) over the points x of alpha
+ * (weights fixed) by `iters` steps of
+ *   x_i <- x_i - lr (1/alpha_i) (1/K) sum_k dS(alpha, beta_k)/dx_i,
+ * each gradient from a solve of sinkhorn_divergence with *params followed by
+ * sinkhorn_grad_x.  With lr = 1 and without the debiasing term this is the
+ * classical fixed-point update x_i <- mean_k of the barycentric projections.
+ *   x: N x D device, updated in place; alpha: N device.
+ *   ys, betas: HOST arrays of K device pointers (M_k x D points, M_k weights);
+ *   Ms: host array of the K sizes.
+ *   S_hist: optional host output of iters + 1 values, the objective
+ *   (1/K) sum_k S(alpha, beta_k) before each step and after the last one.
+ * Errors: those of sinkhorn_divergence, EINVAL for K < 1, iters < 0, lr <= 0.
+ */
+int sinkhorn_barycenter(otgb_ctx *ctx, float *x, const float *alpha, int N, int K, const float *const *ys,
+                        const float *const *betas, const int *Ms, int D, const otgb_params *params, int iters,
+                        double lr, double *S_hist);
 
 /*
  * One softmin sweep of the Algorithm in Section 2, exposed for testing and for

@@ -48,6 +48,7 @@ def _load():
         u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
         ci, cd = C.c_int, C.c_double
         lib.oracle_threads.argtypes = []; lib.oracle_threads.restype = ci
+        lib.oracle_set_threads.argtypes = [ci]; lib.oracle_set_threads.restype = None
         lib.oracle_grad_x.argtypes = [f32p, f32p, ci, f32p, f32p, ci, ci, ci, cd, f64p, f64p, f64p, f64p]
         lib.oracle_grad_x.restype = None
         lib.oracle_cost.argtypes = [f32p, f32p, ci, ci]; lib.oracle_cost.restype = cd
@@ -82,6 +83,11 @@ def _load():
 def threads() -> int:
     """Threads of the oracle's OpenMP row loops (the host cores its timings use)."""
     return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the row loops from now on (timings on one core use 1)."""
+    _load().oracle_set_threads(int(n))
 
 
 def _f32(a):

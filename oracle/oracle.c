@@ -39,6 +39,16 @@ int oracle_threads(void)
 #endif
 }
 
+/* Threads of the row loops from now on (n >= 1), for timings on one core. */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Ground cost, Section 2: C(x, y) = (1/p) |x - y|^p.                          */
 /* ------------------------------------------------------------------------ */

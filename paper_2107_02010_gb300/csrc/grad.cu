@@ -1,0 +1,248 @@
+// Gradient of the debiased Sinkhorn divergence in the points, and the
+// free-support Wasserstein barycenter built on it.
+//
+// Section 2 ("Unbiased Sinkhorn divergences"): at the fixed point, S is a
+// function of the points whose gradient is an expression of the converged
+// duals (envelope theorem).  For the cost C(x, y) = |x - y|^2 / 2,
+//   dS/dx_i = alpha_i [ sum_j beta_j  e^{(f_i + g_j - C(x_i, y_j)) / eps} (x_i - y_j)
+//                     - sum_k alpha_k e^{(a_i + a_k - C(x_i, x_k)) / eps} (x_i - x_k) ],
+// the first sum from OT(alpha, beta), the second from -OT(alpha, alpha)/2 (x_i
+// enters that term twice).  The barycenter ("Track density atlas" of Section 2)
+// moves the support of alpha down the mean gradient of S(alpha, beta_k).
+//
+// Each CTA owns 128 rows (one per thread, the row's point and its gradient in
+// registers); column tiles are staged in shared memory and read as broadcasts.
+// Per pair: the direct difference form of the cost (no cancellation), one
+// ex2, and the weighted difference accumulated with an online maximum (a term
+// larger than every earlier one rescales the running sums), so no shift has
+// to be known in advance.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "solver.cuh"
+
+namespace otgb {
+namespace {
+
+constexpr int kGR = 128;  // rows per CTA, one per thread
+constexpr int kGC = 64;   // columns per shared tile
+
+struct GradPart {
+    const float *cols;  // m x D (caller layout)
+    const float *w;     // m weights
+    const float *pot;   // m potential values
+    int m;
+    float sign;
+};
+
+struct GradArgs {
+    const float *rows;     // n x D (caller layout)
+    const float *row_w;    // n weights
+    const float *rpot[2];  // the row's potential in each part
+    GradPart part[2];
+    int n, D;
+    float s;               // log2(e) / eps
+    float scale;           // multiplies the result
+    int accumulate;        // 1: grad += result, 0: grad = result
+    float *grad;           // n x D
+};
+
+__device__ __forceinline__ float ex2g(float v) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+    return y;
+}
+
+template <int D4>
+__global__ void __launch_bounds__(kGR) grad_kernel(const __grid_constant__ GradArgs A) {
+    __shared__ float ys[kGC][D4];
+    __shared__ float yt[kGC];
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * kGR + t;
+    const bool valid = i < A.n;
+    const int D = A.D;
+    float x[D4], out[D4];
+#pragma unroll
+    for (int d = 0; d < D4; ++d) {
+        x[d] = (valid && d < D) ? A.rows[(size_t)i * D + d] : 0.f;
+        out[d] = 0.f;
+    }
+    for (int q = 0; q < 2; ++q) {
+        const GradPart &P = A.part[q];
+        // base-2 exponent of each term: s f_i + (log2 w_j + s pot_j) - s C_ij
+        const float rt = valid ? A.s * A.rpot[q][i] : 0.f;
+        float m = -INFINITY;
+        float v[D4];
+#pragma unroll
+        for (int d = 0; d < D4; ++d) v[d] = 0.f;
+        for (int c0 = 0; c0 < P.m; c0 += kGC) {
+            const int nc = min(kGC, P.m - c0);
+            __syncthreads();
+            for (int e = t; e < kGC * D4; e += kGR) {
+                const int c = e / D4, d = e - c * D4;
+                ys[c][d] = (c < nc && d < D) ? P.cols[(size_t)(c0 + c) * D + d] : 0.f;
+            }
+            if (t < kGC) {
+                const float w = t < nc ? P.w[c0 + t] : 0.f;
+                yt[t] = w > 0.f ? log2f(w) + A.s * P.pot[c0 + t] : -INFINITY;
+            }
+            __syncthreads();
+            for (int c = 0; c < nc; ++c) {
+                const float ct = yt[c];
+                if (ct == -INFINITY) continue;  // the same column for every thread
+                float sq = 0.f;
+#pragma unroll
+                for (int d = 0; d < D4; ++d) {
+                    const float df = x[d] - ys[c][d];
+                    sq = fmaf(df, df, sq);
+                }
+                const float e = fmaf(-0.5f * A.s, sq, rt + ct);
+                if (e > m) {  // rescale the running sums to the new maximum
+                    const float sc = ex2g(m - e);
+#pragma unroll
+                    for (int d = 0; d < D4; ++d) v[d] *= sc;
+                    m = e;
+                }
+                const float w = ex2g(e - m);
+#pragma unroll
+                for (int d = 0; d < D4; ++d) v[d] = fmaf(w, x[d] - ys[c][d], v[d]);
+            }
+        }
+        // the part's sum is 2^m v (m = -inf: no term, nothing to add)
+        if (m > -INFINITY) {
+            const float em = P.sign * exp2f(m);
+#pragma unroll
+            for (int d = 0; d < D4; ++d) out[d] = fmaf(em, v[d], out[d]);
+        }
+    }
+    if (!valid) return;
+    const float aw = A.row_w[i] * A.scale;
+    for (int d = 0; d < D; ++d) {
+        float r = aw * out[d];
+        if (A.accumulate) r += A.grad[(size_t)i * D + d];
+        A.grad[(size_t)i * D + d] = r;
+    }
+}
+
+void grad_launch(const GradArgs &A, cudaStream_t st) {
+    const int grid = (A.n + kGR - 1) / kGR;
+    const int D4 = (A.D + 3) & ~3;
+    switch (D4) {
+#define OTGB_GRAD_CASE(K) \
+    case K: grad_kernel<K><<<grid, kGR, 0, st>>>(A); break;
+        OTGB_GRAD_CASE(4) OTGB_GRAD_CASE(8) OTGB_GRAD_CASE(12) OTGB_GRAD_CASE(16)
+        OTGB_GRAD_CASE(20) OTGB_GRAD_CASE(24) OTGB_GRAD_CASE(28) OTGB_GRAD_CASE(32)
+        OTGB_GRAD_CASE(36) OTGB_GRAD_CASE(40) OTGB_GRAD_CASE(44) OTGB_GRAD_CASE(48)
+        OTGB_GRAD_CASE(52) OTGB_GRAD_CASE(56) OTGB_GRAD_CASE(60) OTGB_GRAD_CASE(64)
+#undef OTGB_GRAD_CASE
+        default: throw Error{OTGB_EINTERNAL, "grad_launch: D out of range"};
+    }
+    OTGB_CHECK_LAUNCH();
+}
+
+GradArgs grad_args(const float *x, const float *alpha, int N, const float *y, const float *beta, int M, int D,
+                   double eps, const float *a_self, const float *f, const float *g, float *grad, float scale,
+                   int accumulate) {
+    GradArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.rows = x;
+    A.row_w = alpha;
+    A.rpot[0] = f;       // OT(alpha, beta): f on x against (y, beta, g)
+    A.rpot[1] = a_self;  // OT(alpha, alpha): a on x against (x, alpha, a)
+    A.part[0] = GradPart{y, beta, g, M, 1.f};
+    A.part[1] = GradPart{x, alpha, a_self, N, -1.f};
+    A.n = N;
+    A.D = D;
+    A.s = (float)(1.4426950408889634 / eps);
+    A.scale = scale;
+    A.accumulate = accumulate;
+    A.grad = grad;
+    return A;
+}
+
+// x_i <- x_i - lr G_i / alpha_i (rows with alpha_i = 0 stay)
+__global__ void descent_kernel(float *x, const float *alpha, const float *G, int n, int D, float lr) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)n * D) return;
+    const float w = alpha[e / D];
+    if (w > 0.f) x[e] -= lr * G[e] / w;
+}
+
+}  // namespace
+}  // namespace otgb
+
+using namespace otgb;
+
+extern "C" int sinkhorn_grad_x(otgb_ctx *ctx, const float *x, const float *alpha, int N, const float *y,
+                               const float *beta, int M, int D, int p, double eps, const float *f, const float *g,
+                               const float *a_self, float *grad) {
+    if (!ctx) return fail(nullptr, Error{OTGB_EINVAL, "sinkhorn_grad_x: null context"});
+    try {
+        ctx_set_device(ctx);
+        require(x && alpha && y && beta && f && g && a_self && grad, "sinkhorn_grad_x: null pointer argument");
+        require(N >= 1 && M >= 1, "sinkhorn_grad_x: N and M must be >= 1");
+        require(D >= 1 && D <= 64, "sinkhorn_grad_x: D must be in [1, 64]");
+        require(p == 2, "sinkhorn_grad_x: only p = 2 is supported");
+        require(eps > 0.0 && std::isfinite(eps), "sinkhorn_grad_x: eps must be > 0");
+        cudaStream_t st = ctx_stream(ctx);
+        grad_launch(grad_args(x, alpha, N, y, beta, M, D, eps, a_self, f, g, grad, 1.f, 0), st);
+        OTGB_CUDA_TRY(cudaStreamSynchronize(st));
+        return OTGB_OK;
+    } catch (const Error &e) {
+        return fail(ctx, e);
+    }
+}
+
+extern "C" int sinkhorn_barycenter(otgb_ctx *ctx, float *x, const float *alpha, int N, int K,
+                                   const float *const *ys, const float *const *betas, const int *Ms, int D,
+                                   const otgb_params *params, int iters, double lr, double *S_hist) {
+    if (!ctx) return fail(nullptr, Error{OTGB_EINVAL, "sinkhorn_barycenter: null context"});
+    try {
+        ctx_set_device(ctx);
+        require(x && alpha && ys && betas && Ms, "sinkhorn_barycenter: null pointer argument");
+        require(N >= 1 && K >= 1 && iters >= 0, "sinkhorn_barycenter: N, K >= 1 and iters >= 0 required");
+        require(D >= 1 && D <= 64, "sinkhorn_barycenter: D must be in [1, 64]");
+        require(lr > 0.0 && std::isfinite(lr), "sinkhorn_barycenter: lr must be > 0");
+        otgb_params P;
+        if (params) P = *params;
+        else otgb_default_params(&P);
+        require(P.p == 2, "sinkhorn_barycenter: only p = 2 is supported");
+        for (int k = 0; k < K; ++k) require(ys[k] && betas[k] && Ms[k] >= 1, "sinkhorn_barycenter: bad measure");
+        cudaStream_t st = ctx_stream(ctx);
+        Workspace &ws = ctx_ws(ctx);
+        int Mmax = 0;
+        for (int k = 0; k < K; ++k) Mmax = std::max(Mmax, Ms[k]);
+        // buffers that survive the solves' own workspace use: named apart
+        float *f = ws.get<float>("bary:f", N);
+        float *a = ws.get<float>("bary:a", N);
+        float *g = ws.get<float>("bary:g", Mmax);
+        float *G = ws.get<float>("bary:G", (size_t)N * D);
+        const double eps = P.blur * P.blur;
+        for (int it = 0; it <= iters; ++it) {
+            double Ssum = 0.0;
+            const bool last = it == iters;
+            if (last && !S_hist) break;
+            for (int k = 0; k < K; ++k) {
+                double S = 0.0;
+                const int rc = sinkhorn_divergence(ctx, x, alpha, N, ys[k], betas[k], Ms[k], D, &P, &S, f, g, a,
+                                                   nullptr, nullptr, nullptr);
+                if (rc != OTGB_OK && rc != OTGB_ENOCONV) return rc;  // the message is already set
+                Ssum += S;
+                if (!last)
+                    grad_launch(grad_args(x, alpha, N, ys[k], betas[k], Ms[k], D, eps, a, f, g, G,
+                                          (float)(1.0 / K), k > 0),
+                                st);
+            }
+            if (S_hist) S_hist[it] = Ssum / K;
+            if (last) break;
+            const size_t tot = (size_t)N * D;
+            descent_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, alpha, G, N, D, (float)lr);
+            OTGB_CHECK_LAUNCH();
+        }
+        OTGB_CUDA_TRY(cudaStreamSynchronize(st));
+        return OTGB_OK;
+    } catch (const Error &e) {
+        return fail(ctx, e);
+    }
+}

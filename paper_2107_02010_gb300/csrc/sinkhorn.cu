@@ -89,6 +89,19 @@ int *spatial_sort(otgb_ctx *ctx, const std::string &tag, const float *x, int n, 
     return perm;
 }
 
+// The bounded-wait error path, exercised on purpose (params.debug_wait_probe):
+// one thread polls a device word that nothing writes, pausing between polls,
+// and gives up after `polls` polls by flagging the error word that the
+// tensor-core and tile waits flag when they give up.
+__global__ void wait_probe_kernel(const volatile unsigned *flag, unsigned *err, int polls) {
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < polls; ++k) {
+        if (*flag) return;
+        __nanosleep(1000);
+    }
+    atomicOr(err, 4u);
+}
+
 }  // namespace
 
 // One averaged step of the four instances at temperature eps.
@@ -561,6 +574,12 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         pack_points(y, b, s.Y.perm, M, D, d_cen, s.Y.pts, s.Y.logw, s.Y.w, st);
 
         s.alloc_common();
+        if (P.debug_wait_probe) {
+            unsigned *flag = s.ws->get<unsigned>("probe", 1);
+            OTGB_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(unsigned), st));
+            wait_probe_kernel<<<1, 32, 0, st>>>(flag, s.launch.tc_err, 1000);
+            OTGB_CHECK_LAUNCH();
+        }
         s.alloc_pots(P);
         s.g_from_f = P.init_g_from_f != 0 && P.f_init != nullptr && P.g_init == nullptr;
 
@@ -662,7 +681,7 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         }
         if (rc != OTGB_OK) {
             const char *m = rc == OTGB_ENOCONV   ? "sinkhorn_divergence: max_iters reached before the stopping rule held"
-                            : rc == OTGB_ETIMEOUT ? "sinkhorn_divergence: a bounded tensor-core wait gave up"
+                            : rc == OTGB_ETIMEOUT ? "sinkhorn_divergence: a bounded device wait gave up"
                                                   : "sinkhorn_divergence: a potential or the divergence is not finite";
             return fail(ctx, Error{rc, m});
         }

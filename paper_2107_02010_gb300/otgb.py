@@ -49,6 +49,7 @@ class Params(C.Structure):
         ("rows_per_thread", C.c_int),
         ("init_g_from_f", C.c_int),
         ("warm_max_iters", C.c_int),
+        ("debug_wait_probe", C.c_int),
     ]
 
 
@@ -92,7 +93,7 @@ EXPORTS = ["otgb_default_params", "otgb_create", "otgb_destroy", "otgb_last_erro
            "otgb_mlp_n_params", "otgb_mlp_fit_normalization", "otgb_mlp_set_normalization",
            "otgb_mlp_get_normalization", "otgb_mlp_set_params", "otgb_mlp_get_params", "otgb_mlp_grad",
            "otgb_mlp_adam_step", "otgb_mlp_train_step", "otgb_mlp_train_epoch", "otgb_mlp_infer", "otgb_mlp_save",
-           "otgb_mlp_load", "sinkhorn_divergence_warm"]
+           "otgb_mlp_load", "sinkhorn_divergence_warm", "sinkhorn_grad_x", "sinkhorn_barycenter"]
 
 
 def kernel_launches() -> int:
@@ -156,7 +157,11 @@ def load(build_if_missing: bool = True):
     lib.otgb_mlp_load.argtypes = [vp, C.c_char_p]
     lib.sinkhorn_divergence_warm.argtypes = [vp, vp, vp, vp, ci, vp, vp, ci, ci, C.POINTER(Params), vp,
                                              C.POINTER(cd), vp, vp, vp, vp, C.POINTER(vp), C.POINTER(Stats)]
-    for name in ("otgb_create", "otgb_destroy", "sinkhorn_divergence", "transport_apply", "cluster_grid",
+    lib.sinkhorn_grad_x.argtypes = [vp, vp, vp, ci, vp, vp, ci, ci, ci, cd, vp, vp, vp, vp]
+    lib.sinkhorn_barycenter.argtypes = [vp, vp, vp, ci, ci, C.POINTER(vp), C.POINTER(vp), C.POINTER(ci), ci,
+                                        C.POINTER(Params), ci, cd, C.POINTER(cd)]
+    for name in ("sinkhorn_grad_x", "sinkhorn_barycenter", "otgb_create", "otgb_destroy", "sinkhorn_divergence",
+                 "transport_apply", "cluster_grid",
                  "cluster_kmeans", "otgb_softmin", "otgb_mlp_create", "otgb_mlp_destroy", "otgb_mlp_n_params",
                  "otgb_mlp_fit_normalization", "otgb_mlp_set_normalization", "otgb_mlp_get_normalization",
                  "otgb_mlp_set_params", "otgb_mlp_get_params", "otgb_mlp_grad", "otgb_mlp_adam_step",
@@ -273,6 +278,41 @@ def transport_apply(ctx: Context, plan: Plan, f, g, labels, L, want_scores=True)
     ctx.check(load().transport_apply(ctx.h, plan.h, _f32(f), _f32(g), _ptr(labels), int(L), _ptr(sc), _ptr(am),
                                      _ptr(rm)))
     return sc, am, rm
+
+
+def sinkhorn_grad_x(ctx: Context, x, alpha, y, beta, eps, f, g, a_self, p=2):
+    """dS(alpha, beta)/dx (N x D) from the duals of a solve (sinkhorn_grad_x).
+    For dS/dy call sinkhorn_grad_x(ctx, y, beta, x, alpha, eps, g, f, b_self)."""
+    N, D = x.shape
+    M = y.shape[0]
+    if y.shape[1] != D or alpha.numel() != N or beta.numel() != M:
+        raise ValueError("sinkhorn_grad_x: shapes of x, alpha, y, beta do not match")
+    if f.numel() != N or a_self.numel() != N or g.numel() != M:
+        raise ValueError("sinkhorn_grad_x: f and a_self need N entries, g needs M")
+    grad = torch.empty((N, D), device=x.device, dtype=torch.float32)
+    ctx.check(load().sinkhorn_grad_x(ctx.h, _f32(x), _f32(alpha), N, _f32(y), _f32(beta), M, D, int(p), float(eps),
+                                     _f32(f), _f32(g), _f32(a_self), _ptr(grad)))
+    return grad
+
+
+def sinkhorn_barycenter(ctx: Context, x, alpha, ys, betas, params: Params | None = None, iters=5, lr=1.0):
+    """Free-support barycenter (sinkhorn_barycenter): moves x (N x D, float32,
+    in place) and returns the objective history (iters + 1 values)."""
+    N, D = x.shape
+    K = len(ys)
+    if len(betas) != K or K < 1:
+        raise ValueError("sinkhorn_barycenter: one weight vector per measure")
+    for y, b in zip(ys, betas):
+        if y.dim() != 2 or y.shape[1] != D or b.numel() != y.shape[0]:
+            raise ValueError("sinkhorn_barycenter: each measure needs M x D points and M weights")
+    yp = (C.c_void_p * K)(*[_f32(y).value for y in ys])
+    bp = (C.c_void_p * K)(*[_f32(b).value for b in betas])
+    ms = (C.c_int * K)(*[int(y.shape[0]) for y in ys])
+    hist = (C.c_double * (iters + 1))()
+    p = params if params is not None else default_params()
+    ctx.check(load().sinkhorn_barycenter(ctx.h, _f32(x), _f32(alpha), N, K, yp, bp, ms, D, C.byref(p), int(iters),
+                                         float(lr), hist))
+    return list(hist)
 
 
 def cluster_grid(ctx: Context, x, cell, w=None, want_centroids=True):

@@ -1,0 +1,80 @@
+"""60-D fibers against the converged FP64 oracle.
+
+The oracle's converged solve of one seeded fiber problem (2000 subject fibers
+against 1800 atlas fibers, 20 bundles, blur 2 mm, reach 20 mm, q 0.5; written
+by tests/golden/make_fibers_60d.py, which calls only the oracle and the seeded
+generator) is the reference.  The float32 paths -- dense single scale and the
+coarse-to-fine solve with k-means clusters, kernel truncation and
+extrapolation -- must reach S and all four duals within 1e-5 (Section 2: the
+accelerations change the path to the fixed point, not the fixed point); the
+reduced-precision tensor-core form within 1e-3."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2107_02010_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+FIX = os.path.join(HERE, "golden", "fibers_60d_2000x1800.npz")
+N, M, BLUR, REACH = 2000, 1800, 2.0, 20.0
+
+
+@pytest.fixture(scope="module")
+def case():
+    from paper_2107_02010_gb300 import otgb
+
+    ref = np.load(FIX)
+    ctrl = synth.bundle_centrelines()
+    x, a, _ = synth.fiber_bundles(N, seed=4, ctrl=ctrl, perturb=3.0)
+    y, b, _ = synth.fiber_bundles(M, seed=5, ctrl=ctrl)
+    ctx = otgb.Context()
+    T = lambda v: torch.from_numpy(v).cuda()
+    yield dict(otgb=otgb, ctx=ctx, ref=ref, X=T(x), A=T(a), Y=T(y), B=T(b))
+    ctx.close()
+
+
+def _errors(out, ref):
+    eps = BLUR ** 2
+    e = {"S": abs(out["S"] - float(ref["S"])) / abs(float(ref["S"]))}
+    for k, key in (("f", "f"), ("g", "g"), ("a_self", "a"), ("b_self", "b")):
+        got = out[k].cpu().numpy().astype(np.float64)
+        want = ref[key]
+        e[key] = float(np.max(np.abs(got - want)) / (np.max(np.abs(want)) + eps))
+    return e
+
+
+def _solve(case, **kw):
+    otgb = case["otgb"]
+    p = otgb.default_params(blur=BLUR, reach=REACH, scaling=0.5, tol=1e-9, max_iters=20000, **kw)
+    out = otgb.sinkhorn_divergence(case["ctx"], case["X"], case["A"], case["Y"], case["B"], p, want_self=True)
+    assert out["status"] == 0
+    return out
+
+
+def test_fixture_is_the_stated_problem(case):
+    ref = case["ref"]
+    assert ref["f"].shape == (N,) and ref["g"].shape == (M,)
+    assert float(ref["delta"]) < 1e-12
+
+
+@pytest.mark.parametrize("form", ["dense", "kmeans"])
+def test_fp32_fibers_match_converged_oracle(case, form):
+    kw = dict(precision=2)
+    if form == "kmeans":
+        kw.update(multiscale=1, cluster=1, k_clusters=40, kmeans_iters=10)
+    out = _solve(case, **kw)
+    e = _errors(out, case["ref"])
+    print("\n%s float32: %s, %d steps" % (form, {k: "%.2e" % v for k, v in e.items()}, out["stats"]["iters_total"]))
+    for k, v in e.items():
+        assert v < 1e-5, (form, k, v)
+
+
+def test_tensor_core_fibers_within_reduced_precision_bar(case):
+    out = _solve(case, precision=1, multiscale=1, cluster=1, k_clusters=40, kmeans_iters=10)
+    e = _errors(out, case["ref"])
+    print("\ntensor-core: %s" % {k: "%.2e" % v for k, v in e.items()})
+    for k, v in e.items():
+        assert v < 1e-3, (k, v)
