@@ -79,9 +79,11 @@ def fiber_data(n):
 
 
 def fiber_params(otgb, n, precision, tol, max_iters):
+    # the stopping rule is evaluated every 3 steps (a check costs one FP64 sum
+    # and one host read, far below a step of this size)
     return otgb.default_params(blur=2.0, reach=20.0, scaling=0.5, multiscale=1, cluster=1,
                                k_clusters=max(20, n // 1000), kmeans_iters=10, tol=tol, max_iters=max_iters,
-                               precision=precision)
+                               precision=precision, check_every=3)
 
 
 def density_data(args):

@@ -17,8 +17,11 @@
  *    a message.  No exception crosses the ABI and no kernel traps.
  *  - Scratch memory comes from the context (stream-ordered allocations that
  *    grow on demand) and is released by otgb_destroy().
- *  - Ground cost: C(x, y) = |x - y|^2 / 2 (p = 2, Section 2).  Other p are
- *    rejected with OTGB_EINVAL.  1 <= D <= 64.
+ *  - Ground cost: C(x, y) = |x - y|^p / p (Section 2) with p = 2 (the default,
+ *    every engine) or p = 1 (C = |x - y|: sinkhorn_divergence on the CUDA cores,
+ *    float32, direct form with a square root per pair; sinkhorn_grad_x;
+ *    sinkhorn_barycenter).  eps = blur^p, rho = reach^p.  Other p are rejected
+ *    with OTGB_EINVAL.  1 <= D <= 64.
  */
 #ifndef OTGB_H
 #define OTGB_H
@@ -57,7 +60,8 @@ typedef struct otgb_plan otgb_plan; /* result of a solve, reused by transport_ap
 
 /* Solver parameters (Section 2: blur, reach, scaling; p = 2). */
 typedef struct {
-    int p;                 /* exponent of the cost; must be 2 */
+    int p;                 /* exponent of the cost |x - y|^p / p: 2 (default) or 1 (precision FP32 or
+                              FP32_SIMT only; label transfer needs p = 2) */
     double blur;           /* finest scale sigma; eps = blur^p.  > 0 */
     double reach;          /* rho = reach^p; <= 0 or +inf: balanced OT (lambda = 1) */
     double scaling;        /* q in (0,1): sigma_{k+1} = q sigma_k (the paper's default is 0.9) */
@@ -100,6 +104,14 @@ typedef struct {
                               flags the error word that the tensor-core and tile waits use, and the solve
                               (whose outputs are still written) returns OTGB_ETIMEOUT.  Nothing faults or
                               hangs and the context stays usable.  0 = off (default). */
+    int polish;            /* D > 3 only: 1 = once the stopping rule holds, run the loop at blur again, to the
+                              same rule, with every softmin in the direct difference form of the cost
+                              (sum of squared coordinate differences, FP32 CUDA cores, about twice the work
+                              per pair).  The fast forms add terms as large as the spread of a row block
+                              times the distance of a column, whose rounding, amplified along the slowly
+                              contracting bundle modes of unbalanced problems, leaves the duals a few 1e-5
+                              from the fixed point on multi-bundle fiber problems while S is exact to ~1e-8;
+                              the polish brings the duals to the float32 level.  0 = off (default). */
 } otgb_params;
 
 /* Statistics of one solve (host struct, filled when non-null). */
@@ -162,7 +174,7 @@ const char *otgb_last_error(const otgb_ctx *ctx);
  *     otgb_plan_free).  The plan keeps NON-OWNING views of x, y and b: they must
  *     stay valid until the plan is freed.
  *   stats: optional host struct.
- * Errors: EINVAL for N or M < 1, D outside [1, 64], p != 2, blur <= 0, q outside
+ * Errors: EINVAL for N or M < 1, D outside [1, 64], p not in {1, 2}, blur <= 0, q outside
  * (0,1), negative or non-finite weights or a zero total mass; ENOCONV when
  * max_iters ends the loop first (outputs are written); ENONFINITE when a
  * potential turns NaN/Inf; ECUDA/ENOMEM from the runtime.
@@ -181,11 +193,37 @@ int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a, int N, co
  *     -1 when the row is empty), row_mass: N float32 = sum_l Lab_il (optional).
  * A row whose mass is near 0 is an outlier (Section 2, label transfer).
  * The sum runs over all atlas points (dense), for any 1 <= D <= 64.
- * Errors: EINVAL for a null plan, L < 1 or L > 1024, null f/g/labels/argmax.
+ * Errors: EINVAL for a null plan, a plan of a p = 1 solve, L < 1 or L > 1024, null f/g/labels/argmax.
  */
 int transport_apply(otgb_ctx *ctx, const otgb_plan *plan, const float *f, const float *g, const int32_t *labels,
                     int L, float *scores, int32_t *argmax, float *row_mass);
 void otgb_plan_free(otgb_plan *plan);
+
+/*
+ * Flip augmentation of a fiber tractogram (Section 2, fiber encoding: fibers
+ * resampled to P points are points of R^{3P}; their orientation is arbitrary,
+ * so the tractogram is augmented with the mirror flip of every fiber).
+ *   x: N x 3P device (fiber i = its P points (x, y, z) in order).
+ *   out: 2N x 3P device output: rows 0..N-1 are the fibers, row N + i is fiber
+ *   i with its points in reverse order (each point unchanged).
+ * Solve and transfer labels on the augmented rows (weights: one per row),
+ * then pick one version per fiber with otgb_select_flips.
+ * Errors: EINVAL for null pointers, N < 1, P < 1 or 3P > 64.
+ */
+int otgb_flip_fibers(otgb_ctx *ctx, const float *x, int N, int P, float *out);
+
+/*
+ * The matched version of each fiber after transport_apply on flip-augmented
+ * rows (Section 2, label transfer: the plan on the augmented data matches one
+ * version of each fiber, and only that one is kept): of rows i and N + i, the
+ * one with the larger row mass (ties: the original).
+ *   row_mass (2N), argmax (2N): transport_apply's outputs on the 2N rows (device).
+ *   label (N, required), version (N, optional; 0 = original, 1 = flip),
+ *   mass (N, optional; the kept row mass, for outlier detection): device outputs.
+ * Errors: EINVAL for null required pointers or N < 1.
+ */
+int otgb_select_flips(otgb_ctx *ctx, const float *row_mass, const int32_t *argmax, int N, int32_t *label,
+                      int32_t *version, float *mass);
 
 /*
  * Grid clustering (coarse subsampling, Section 2): cell coordinate
@@ -219,10 +257,11 @@ int cluster_kmeans(otgb_ctx *ctx, const float *x, const float *w, int N, int D, 
 /*
  * Gradient of the debiased divergence in the points of the first measure
  * (Section 2, "Unbiased Sinkhorn divergences": at the fixed point the
- * gradients of S are expressions of the dual vectors).  For the cost
- * C(x, y) = |x - y|^2 / 2:
- *   grad_i = alpha_i [ sum_j beta_j  exp((f_i + g_j - C(x_i, y_j)) / eps) (x_i - y_j)
- *                    - sum_k alpha_k exp((a_i + a_k - C(x_i, x_k)) / eps) (x_i - x_k) ]
+ * gradients of S are expressions of the dual vectors).  With
+ * G(u, v) = grad_u C(u, v) = u - v for p = 2 and (u - v) / |u - v| for p = 1
+ * (0 at u = v):
+ *   grad_i = alpha_i [ sum_j beta_j  exp((f_i + g_j - C(x_i, y_j)) / eps) G(x_i, y_j)
+ *                    - sum_k alpha_k exp((a_i + a_k - C(x_i, x_k)) / eps) G(x_i, x_k) ]
  * = dS_{eps,rho}(alpha, beta) / dx_i, with (f, g) the dual pair of
  * OT(alpha, beta) and a the symmetric dual of OT(alpha, alpha) that
  * sinkhorn_divergence wrote (f, g, a_self; caller order) at eps = blur^p.
@@ -232,7 +271,7 @@ int cluster_kmeans(otgb_ctx *ctx, const float *x, const float *w, int N, int D, 
  *   grad: N x D device output (float32).
  * Dense: every pair is summed (the direct difference form of the cost, FP32,
  * with a running maximum per row), for any 1 <= D <= 64.
- * Errors: EINVAL for null pointers, sizes < 1, D outside [1, 64], p != 2, eps <= 0.
+ * Errors: EINVAL for null pointers, sizes < 1, D outside [1, 64], p not in {1, 2}, eps <= 0.
  */
 int sinkhorn_grad_x(otgb_ctx *ctx, const float *x, const float *alpha, int N, const float *y, const float *beta,
                     int M, int D, int p, double eps, const float *f, const float *g, const float *a_self,
@@ -244,8 +283,8 @@ int sinkhorn_grad_x(otgb_ctx *ctx, const float *x, const float *alpha, int N, co
  * (weights fixed) by `iters` steps of
  *   x_i <- x_i - lr (1/alpha_i) (1/K) sum_k dS(alpha, beta_k)/dx_i,
  * each gradient from a solve of sinkhorn_divergence with *params followed by
- * sinkhorn_grad_x.  With lr = 1 and without the debiasing term this is the
- * classical fixed-point update x_i <- mean_k of the barycentric projections.
+ * sinkhorn_grad_x.  With p = 2, lr = 1 and without the debiasing term this is
+ * the classical fixed-point update x_i <- mean_k of the barycentric projections.
  *   x: N x D device, updated in place; alpha: N device.
  *   ys, betas: HOST arrays of K device pointers (M_k x D points, M_k weights);
  *   Ms: host array of the K sizes.

@@ -49,6 +49,8 @@ def _load():
         ci, cd = C.c_int, C.c_double
         lib.oracle_threads.argtypes = []; lib.oracle_threads.restype = ci
         lib.oracle_set_threads.argtypes = [ci]; lib.oracle_set_threads.restype = None
+        lib.oracle_flip_fibers.argtypes = [f32p, ci, ci, f32p]; lib.oracle_flip_fibers.restype = None
+        lib.oracle_select_flips.argtypes = [f64p, i32p, ci, i32p, i32p, f64p]; lib.oracle_select_flips.restype = None
         lib.oracle_grad_x.argtypes = [f32p, f32p, ci, f32p, f32p, ci, ci, ci, cd, f64p, f64p, f64p, f64p]
         lib.oracle_grad_x.restype = None
         lib.oracle_cost.argtypes = [f32p, f32p, ci, ci]; lib.oracle_cost.restype = cd
@@ -199,6 +201,25 @@ def transport_apply(x, y, beta, eps, f, g, labels, L, p=2):
     _load().oracle_transport_apply(x, N, y, _f32(beta), y.shape[0], x.shape[1], int(p), float(eps), _f64(f),
                                    _f64(g), np.ascontiguousarray(labels, np.int32), int(L), sc, am, rm)
     return sc, am, rm
+
+
+def flip_fibers(x, P=20):
+    """2N x 3P: the N fibers, then their mirror flips (points in reverse order)."""
+    x = _f32(x)
+    N = x.shape[0]
+    out = np.empty((2 * N, x.shape[1]), np.float32)
+    _load().oracle_flip_fibers(x, N, int(P), out)
+    return out
+
+
+def select_flips(row_mass, argmax, N):
+    """Per fiber: (label, version 0/1, row mass) of the version with the larger
+    row mass among rows i and N + i of flip-augmented data."""
+    label = np.empty(N, np.int32)
+    version = np.empty(N, np.int32)
+    mass = np.empty(N, np.float64)
+    _load().oracle_select_flips(_f64(row_mass), np.ascontiguousarray(argmax, np.int32), int(N), label, version, mass)
+    return label, version, mass
 
 
 def cluster_grid(x, cell):

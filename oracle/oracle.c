@@ -492,3 +492,35 @@ void oracle_grad_x(const float *x, const float *alpha, int N, const float *y, co
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Flip augmentation (Section 2, fiber encoding): a fiber of P points in 3-D  */
+/* is one point of R^{3P}; rows 0..N-1 of out are the fibers, rows N..2N-1    */
+/* their mirror flips (the P points in reverse order, each point unchanged). */
+/* ------------------------------------------------------------------------ */
+void oracle_flip_fibers(const float *x, int N, int P, float *out)
+{
+    const int D = 3 * P;
+    for (int i = 0; i < N; ++i) {
+        for (int d = 0; d < D; ++d) out[(size_t)i * D + d] = x[(size_t)i * D + d];
+        for (int k = 0; k < P; ++k)
+            for (int c = 0; c < 3; ++c)
+                out[(size_t)(N + i) * D + 3 * k + c] = x[(size_t)i * D + 3 * (P - 1 - k) + c];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Label transfer on flip-augmented data (Section 2, label transfer): the plan */
+/* matches one version of each fiber; of rows i and N+i the one with the       */
+/* larger row mass (ties: the original) gives fiber i its label and mass.      */
+/* ------------------------------------------------------------------------ */
+void oracle_select_flips(const double *row_mass, const int32_t *argmax, int N, int32_t *label, int32_t *version,
+                         double *mass)
+{
+    for (int i = 0; i < N; ++i) {
+        const int v = row_mass[N + i] > row_mass[i] ? 1 : 0;
+        version[i] = v;
+        label[i] = argmax[v * N + i];
+        mass[i] = row_mass[v * N + i];
+    }
+}

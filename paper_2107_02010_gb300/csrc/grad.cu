@@ -42,6 +42,7 @@ struct GradArgs {
     const float *rpot[2];  // the row's potential in each part
     GradPart part[2];
     int n, D;
+    int p1;                // 1: cost |x - y|, gradient (x - y) / |x - y|; 0: cost |x - y|^2 / 2
     float s;               // log2(e) / eps
     float scale;           // multiplies the result
     int accumulate;        // 1: grad += result, 0: grad = result
@@ -97,14 +98,16 @@ __global__ void __launch_bounds__(kGR) grad_kernel(const __grid_constant__ GradA
                     const float df = x[d] - ys[c][d];
                     sq = fmaf(df, df, sq);
                 }
-                const float e = fmaf(-0.5f * A.s, sq, rt + ct);
+                const float dist = A.p1 ? sqrtf(sq) : 0.f;
+                const float e = A.p1 ? fmaf(-A.s, dist, rt + ct) : fmaf(-0.5f * A.s, sq, rt + ct);
                 if (e > m) {  // rescale the running sums to the new maximum
                     const float sc = ex2g(m - e);
 #pragma unroll
                     for (int d = 0; d < D4; ++d) v[d] *= sc;
                     m = e;
                 }
-                const float w = ex2g(e - m);
+                float w = ex2g(e - m);
+                if (A.p1) w = dist > 0.f ? w / dist : 0.f;  // grad_1 |x - y| = (x - y) / |x - y|
 #pragma unroll
                 for (int d = 0; d < D4; ++d) v[d] = fmaf(w, x[d] - ys[c][d], v[d]);
             }
@@ -142,8 +145,8 @@ void grad_launch(const GradArgs &A, cudaStream_t st) {
 }
 
 GradArgs grad_args(const float *x, const float *alpha, int N, const float *y, const float *beta, int M, int D,
-                   double eps, const float *a_self, const float *f, const float *g, float *grad, float scale,
-                   int accumulate) {
+                   int p, double eps, const float *a_self, const float *f, const float *g, float *grad,
+                   float scale, int accumulate) {
     GradArgs A;
     std::memset(&A, 0, sizeof(A));
     A.rows = x;
@@ -154,6 +157,7 @@ GradArgs grad_args(const float *x, const float *alpha, int N, const float *y, co
     A.part[1] = GradPart{x, alpha, a_self, N, -1.f};
     A.n = N;
     A.D = D;
+    A.p1 = p == 1 ? 1 : 0;
     A.s = (float)(1.4426950408889634 / eps);
     A.scale = scale;
     A.accumulate = accumulate;
@@ -183,10 +187,10 @@ extern "C" int sinkhorn_grad_x(otgb_ctx *ctx, const float *x, const float *alpha
         require(x && alpha && y && beta && f && g && a_self && grad, "sinkhorn_grad_x: null pointer argument");
         require(N >= 1 && M >= 1, "sinkhorn_grad_x: N and M must be >= 1");
         require(D >= 1 && D <= 64, "sinkhorn_grad_x: D must be in [1, 64]");
-        require(p == 2, "sinkhorn_grad_x: only p = 2 is supported");
+        require(p == 1 || p == 2, "sinkhorn_grad_x: p must be 1 or 2");
         require(eps > 0.0 && std::isfinite(eps), "sinkhorn_grad_x: eps must be > 0");
         cudaStream_t st = ctx_stream(ctx);
-        grad_launch(grad_args(x, alpha, N, y, beta, M, D, eps, a_self, f, g, grad, 1.f, 0), st);
+        grad_launch(grad_args(x, alpha, N, y, beta, M, D, p, eps, a_self, f, g, grad, 1.f, 0), st);
         OTGB_CUDA_TRY(cudaStreamSynchronize(st));
         return OTGB_OK;
     } catch (const Error &e) {
@@ -207,7 +211,7 @@ extern "C" int sinkhorn_barycenter(otgb_ctx *ctx, float *x, const float *alpha, 
         otgb_params P;
         if (params) P = *params;
         else otgb_default_params(&P);
-        require(P.p == 2, "sinkhorn_barycenter: only p = 2 is supported");
+        require(P.p == 1 || P.p == 2, "sinkhorn_barycenter: p must be 1 or 2");
         for (int k = 0; k < K; ++k) require(ys[k] && betas[k] && Ms[k] >= 1, "sinkhorn_barycenter: bad measure");
         cudaStream_t st = ctx_stream(ctx);
         Workspace &ws = ctx_ws(ctx);
@@ -218,7 +222,7 @@ extern "C" int sinkhorn_barycenter(otgb_ctx *ctx, float *x, const float *alpha, 
         float *a = ws.get<float>("bary:a", N);
         float *g = ws.get<float>("bary:g", Mmax);
         float *G = ws.get<float>("bary:G", (size_t)N * D);
-        const double eps = P.blur * P.blur;
+        const double eps = P.p == 1 ? P.blur : P.blur * P.blur;
         for (int it = 0; it <= iters; ++it) {
             double Ssum = 0.0;
             const bool last = it == iters;
@@ -230,7 +234,7 @@ extern "C" int sinkhorn_barycenter(otgb_ctx *ctx, float *x, const float *alpha, 
                 if (rc != OTGB_OK && rc != OTGB_ENOCONV) return rc;  // the message is already set
                 Ssum += S;
                 if (!last)
-                    grad_launch(grad_args(x, alpha, N, ys[k], betas[k], Ms[k], D, eps, a, f, g, G,
+                    grad_launch(grad_args(x, alpha, N, ys[k], betas[k], Ms[k], D, P.p, eps, a, f, g, G,
                                           (float)(1.0 / K), k > 0),
                                 st);
             }

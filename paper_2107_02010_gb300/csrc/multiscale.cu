@@ -76,6 +76,7 @@ struct MaskInst {
 struct MaskLaunch {
     MaskInst inst[4];
     int D, stride, nwords;
+    int p1;  // 1: cost |x - y| (lower bound gap), else |x - y|^2 / 2 (gap^2 / 2)
     float eps, tau;
 };
 
@@ -99,7 +100,7 @@ __global__ void mask_kernel(const __grid_constant__ MaskLaunch M) {
         float d2 = 0.f;
         for (int d = 0; d < M.D; ++d) { const float t = cI[d] - cJ[d]; d2 = fmaf(t, t, d2); }
         const float gap = fmaxf(sqrtf(d2) - rI - P.rad_c[J], 0.f);
-        return comp(P.max_c[J], P.col_sel) - 0.5f * gap * gap + rowterm;
+        return comp(P.max_c[J], P.col_sel) - (M.p1 ? gap : 0.5f * gap * gap) + rowterm;
     };
     float bm = -INFINITY;
     for (int J = threadIdx.x; J < P.ncl_c; J += blockDim.x) bm = fmaxf(bm, bound(J));
@@ -250,8 +251,14 @@ __global__ void log_kernel(const float *m, int n, float *out) {
 
 // Row blocks of at most `br` rows made of consecutive clusters; a cluster
 // larger than br is cut into pieces.  Writes starts (nblk + 1) and the
-// cluster range of each block.
-void group_blocks(const std::vector<int> &off, int br, std::vector<int> &starts, std::vector<int> &cl) {
+// cluster range of each block.  merge = false keeps one cluster per block:
+// consecutive k-means clusters need not be neighbours, and a block that spans
+// two distant clusters (two fiber bundles) has a large spread around its
+// centre, which the dot-product form of the cost turns into rounding error
+// (the terms s |x - c|^2 / 2 grow with the spread while the exponent of a
+// relevant pair stays small).  Grid cells in Morton order are neighbours, so
+// the grid blocks merge.
+void group_blocks(const std::vector<int> &off, int br, bool merge, std::vector<int> &starts, std::vector<int> &cl) {
     starts.clear();
     cl.clear();
     const int ncl = (int)off.size() - 1;
@@ -269,7 +276,8 @@ void group_blocks(const std::vector<int> &off, int br, std::vector<int> &starts,
         }
         const int first = c;
         int rows = 0;
-        while (c < ncl && off[c + 1] - off[c] <= br && rows + (off[c + 1] - off[c]) <= br) {
+        while (c < ncl && off[c + 1] - off[c] <= br && rows + (off[c + 1] - off[c]) <= br &&
+               (merge || c == first)) {
             rows += off[c + 1] - off[c];
             ++c;
         }
@@ -362,8 +370,9 @@ int Multiscale::run_schedule(Solver &s, const otgb_params &P, const std::vector<
     }
 
     // fine row blocks made of consecutive clusters
-    group_blocks(s.X_off, block_rows, hbx, hclx);
-    group_blocks(s.Y_off, block_rows, hby, hcly);
+    const bool merge = P.cluster == OTGB_CLUSTER_GRID;
+    group_blocks(s.X_off, block_rows, merge, hbx, hclx);
+    group_blocks(s.Y_off, block_rows, merge, hby, hcly);
     d_clx = ws.get<int>("ms:clx", hclx.size());
     d_cly = ws.get<int>("ms:cly", hcly.size());
     OTGB_CUDA_TRY(cudaMemcpyAsync(d_clx, hclx.data(), sizeof(int) * hclx.size(), cudaMemcpyHostToDevice, st));
@@ -381,6 +390,7 @@ int Multiscale::run_schedule(Solver &s, const otgb_params &P, const std::vector<
         cs.st = st;
         cs.ws = s.ws;
         cs.D = D;
+        cs.p = s.p;
         cs.reach = s.reach;
         cs.rho = s.rho;
         cs.timing = false;
@@ -402,7 +412,7 @@ int Multiscale::run_schedule(Solver &s, const otgb_params &P, const std::vector<
         // extrapolation: one softmin per dual, points against the cluster measures,
         // at the first fine scale (or blur when the schedule ended coarse)
         const double sig = k < sched.size() ? sched[k] : P.blur;
-        const double eps = sig * sig;
+        const double eps = s.eps_of(sig);
         SoftminLaunch E = s.launch;  // fallback buffers, counters
         E.use_tcc = 0;
         E.eps = (float)eps;
@@ -413,7 +423,7 @@ int Multiscale::run_schedule(Solver &s, const otgb_params &P, const std::vector<
         E.part = nullptr;
         E.fin = nullptr;
         E.n_fin = 0;
-        const float lam = (float)lambda_of(sig, s.reach);
+        const float lam = (float)s.lam_of(sig);
         const Cloud *ccols[4] = {&cs.X, &cs.Y, &cs.X, &cs.Y};
         const float *cpot[4] = {cs.pa[cs.cur], cs.pb[cs.cur], cs.pf[cs.cur], cs.pg[cs.cur]};
         float *outp[4] = {s.pa[s.cur], s.pb[s.cur], s.pg[s.cur], s.pf[s.cur]};
@@ -460,7 +470,7 @@ void Multiscale::before_fine_step(Solver &s, double sigma) {
     cudaStream_t st = s.st;
     Workspace &ws = *s.ws;
     const int D = s.D, stride = s.X.stride;
-    const float eps = (float)(sigma * sigma);
+    const float eps = (float)s.eps_of(sigma);
     const int c = s.cur;
     // cluster maxima of the current duals
     float4 *mx = ws.get<float4>("ms:maxx", ncl_x);
@@ -482,7 +492,8 @@ void Multiscale::before_fine_step(Solver &s, double sigma) {
     M.nwords = nwords;
     M.eps = eps;
     M.tau = (float)tau;
-    const float inv_lam = (float)(1.0 / lambda_of(sigma, s.reach));
+    M.p1 = s.p == 1 ? 1 : 0;
+    const float inv_lam = (float)(1.0 / s.lam_of(sigma));
     unsigned *bits = ws.get<unsigned>("ms:bits", (size_t)4 * ncmax * nwords);
     // inst 0: rows x, cols x (a); 1: rows y, cols y (b); 2: rows y, cols x (g from f); 3: rows x, cols y (f from g)
     const float *cr[4] = {cen_x, cen_y, cen_y, cen_x}, *cc[4] = {cen_x, cen_y, cen_x, cen_y};
@@ -547,7 +558,7 @@ void Multiscale::before_fine_step(Solver &s, double sigma) {
         dense += (double)I.n_rows * I.n_cols;
     }
     last_kept_fraction = dense > 0 ? kept / dense : 1.0;
-    s.set_work(ncols, D <= 3);
+    s.set_work(ncols, D <= 3 && s.p == 2);
 }
 
 void Multiscale::setup_tcc(Solver &s) {

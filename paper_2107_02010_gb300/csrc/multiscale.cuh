@@ -7,9 +7,10 @@
 
 #include "anderson.cuh"
 #include "otgb_internal.cuh"
+#include "solver.cuh"
 
 struct otgb_plan {
-    int N = 0, M = 0, D = 0;
+    int N = 0, M = 0, D = 0, p = 2;
     const float *x = nullptr, *y = nullptr, *b = nullptr;  // non-owning views
     double eps = 0.0;
 };
@@ -35,7 +36,10 @@ struct Solver {
     cudaStream_t st = nullptr;
     Workspace *ws = nullptr;
     int D = 0;
+    int p = 2;  // exponent of the cost |x - y|^p / p (1 or 2)
     double reach = 0.0, rho = 0.0;
+    double eps_of(double sigma) const { return p == 1 ? sigma : sigma * sigma; }
+    double lam_of(double sigma) const { return lambda_of(sigma, reach, p); }
     Cloud X, Y;
     std::vector<int> X_off, Y_off;  // cluster offsets (host) of the internal order, when clustered
     // the four duals of parity k live in one buffer Z[k] = (a | f | b | g)

@@ -175,6 +175,8 @@ struct SoftminLaunch {
     int use_tc;              // 1: D >= 16 cross term on the tensor cores (BF16 hi/lo split, FP32 accumulate)
     int use_tc3;             // 1: D <= 3 exponent on the tensor cores (three-piece BF16, float32 accuracy)
     int use_tcc;             // 1 (with use_tc): the cluster-tiled tensor-core form (tcc_* fields of the instances)
+    int cost_p1;             // 1: cost |x - y| (p = 1, direct form, softmin_direct.cu); 0: |x - y|^2 / 2
+    int direct;              // 1: the direct difference form for p = 2 as well (softmin_direct.cu)
     int tcc_nwords;          // words of keep bits per row cluster
     unsigned int *tc_err;    // set when a bounded wait (tensor core or tile barrier) gave up (may be null)
     const int4 *fin;         // finalize list (split mode)
@@ -198,6 +200,9 @@ struct SoftminLaunch {
 // D selects the specialisation.  Errors throw otgb::Error.
 void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_t st);
 
+// Softmin in the direct difference form (softmin_direct.cu), cost |x - y| (cost_p1) or
+// |x - y|^2 / 2: any D, blocks <= 128 rows, no split blocks.
+void softmin_direct_launch(const SoftminLaunch &L, int D, cudaStream_t st);
 // Tensor-core softmin (softmin_tc.cu), D >= 16, old values required, blocks <= 128 rows.
 void softmin_tc_launch(const SoftminLaunch &L, int D, cudaStream_t st);
 // Tensor-core D <= 3 softmin at float32 accuracy (softmin3_tc.cu): old values required,

@@ -106,12 +106,12 @@ __global__ void wait_probe_kernel(const volatile unsigned *flag, unsigned *err, 
 
 // One averaged step of the four instances at temperature eps.
 void Solver::step(double sigma, bool count_pairs) {
-    const double eps = sigma * sigma;
+    const double eps = eps_of(sigma);
     SoftminLaunch &L = launch;
     L.eps = (float)eps;
     L.s = (float)(1.4426950408889634 / eps);
     L.eps_ln2 = eps * 0.69314718055994530942;
-    const float lam = (float)lambda_of(sigma, reach);
+    const float lam = (float)lam_of(sigma);
     const int c = cur, n = cur ^ 1;
     // alpha <-> alpha: a~ on x from (x, alpha, a)
     L.inst[0].col_pot = pa[c]; L.inst[0].row_old = pa[c]; L.inst[0].row_out = pa[n];
@@ -221,7 +221,7 @@ void Solver::setup_dense_instances(int block_rows) {
     std::vector<std::vector<int>> ncols(4);
     const int rows_x[4] = {1, 0, 0, 1};
     for (int k = 0; k < 4; ++k) ncols[k].assign(rows_x[k] ? nblk_x : nblk_y, launch.inst[k].n_cols);
-    set_work(ncols, D <= 3);
+    set_work(ncols, D <= 3 && p == 2);
 }
 
 // Items (inst, blk, cb, ce): a block's columns are cut into chunks of CH
@@ -302,6 +302,7 @@ void Solver::alloc_common() {
     OTGB_CUDA_TRY(cudaMemsetAsync(launch.tc_err, 0, sizeof(unsigned), st));
     launch.use_tc = use_tc ? 1 : 0;
     launch.use_tc3 = use_tc3 ? 1 : 0;
+    launch.cost_p1 = p == 1 ? 1 : 0;
     OTGB_CUDA_TRY(cudaMemsetAsync(d_fb_total, 0, sizeof(unsigned long long), st));
     OTGB_CUDA_TRY(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
     if (timing && ev_pool.empty()) {
@@ -392,7 +393,7 @@ bool Solver::potentials_converged(double delta_prev, double delta, int m, double
 }
 
 int Solver::iterate_at_blur(const otgb_params &P, int it_budget) {
-    const double eps = P.blur * P.blur;
+    const double eps = eps_of(P.blur);
     if (P.fixed_iters > 0) {
         for (int k = 0; k < P.fixed_iters && steps < P.max_iters; ++k) fine_step(P.blur);
         S = divergence(eps);
@@ -430,7 +431,7 @@ int Solver::iterate_at_blur(const otgb_params &P, int it_budget) {
 // LSE_i(log alpha_i + (f_i - C(x_i, y_j)) / eps), over the kept columns of the
 // current work (all columns when dense).
 void Solver::sweep_g(double sigma) {
-    const double eps = sigma * sigma;
+    const double eps = eps_of(sigma);
     SoftminLaunch E = launch;
     E.eps = (float)eps;
     E.s = (float)(1.4426950408889634 / eps);
@@ -439,7 +440,7 @@ void Solver::sweep_g(double sigma) {
     I.col_pot = pf[cur];
     I.row_old = nullptr;
     I.row_out = pg[cur];
-    I.lam = (float)lambda_of(sigma, reach);
+    I.lam = (float)lam_of(sigma);
     I.omega = 1.0f;
     require(work_ncols.size() == 4, "sweep_g: no work decomposition", OTGB_EINTERNAL);
     std::vector<int4> items;
@@ -492,13 +493,13 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         require(x && a && y && b && cost_host && f && g, "sinkhorn_divergence: null pointer argument");
         require(N >= 1 && M >= 1, "sinkhorn_divergence: N and M must be >= 1");
         require(D >= 1 && D <= 64, "sinkhorn_divergence: D must be in [1, 64]");
-        require(P.p == 2, "sinkhorn_divergence: only p = 2 is supported");
+        require(P.p == 1 || P.p == 2, "sinkhorn_divergence: p must be 1 or 2");
         require(P.blur > 0.0 && std::isfinite(P.blur), "sinkhorn_divergence: blur must be > 0");
         require(P.scaling > 0.0 && P.scaling < 1.0, "sinkhorn_divergence: scaling must be in (0, 1)");
         require(P.max_iters >= 1, "sinkhorn_divergence: max_iters must be >= 1");
         require(P.precision == OTGB_FP32 || P.precision == OTGB_FP32_SIMT ||
-                    (P.precision == OTGB_TC_BF16X3 && D >= 16),
-                "sinkhorn_divergence: precision must be FP32, FP32_SIMT, or TC_BF16X3 with D >= 16");
+                    (P.precision == OTGB_TC_BF16X3 && D >= 16 && P.p == 2),
+                "sinkhorn_divergence: precision must be FP32, FP32_SIMT, or TC_BF16X3 with D >= 16 and p = 2");
         if (plan_out) *plan_out = nullptr;
 
         Solver s;
@@ -506,12 +507,13 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         s.st = ctx_stream(ctx);
         s.ws = &ctx_ws(ctx);
         s.D = D;
+        s.p = P.p;
         s.reach = P.reach;
-        s.rho = (!(P.reach > 0.0) || std::isinf(P.reach)) ? INFINITY : P.reach * P.reach;
+        s.rho = (!(P.reach > 0.0) || std::isinf(P.reach)) ? INFINITY : std::pow(P.reach, (double)P.p);
         s.timing = stats != nullptr;
         s.translation = P.translation != 0;
-        s.use_tc = P.precision == OTGB_TC_BF16X3 && D >= 16;
-        s.use_tc3 = P.precision == OTGB_FP32 && D <= 3;
+        s.use_tc = P.precision == OTGB_TC_BF16X3 && D >= 16 && P.p == 2;
+        s.use_tc3 = P.precision == OTGB_FP32 && D <= 3 && P.p == 2;
         cudaStream_t st = s.st;
         OTGB_CUDA_TRY(cudaEventRecord(ctx_event(ctx, 0), st));
 
@@ -614,8 +616,17 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
             for (size_t k = 0; k < sched.size() && s.steps < P.max_iters; ++k) s.fine_step(sched[k]);
         }
         if (rc == OTGB_OK) rc = s.iterate_at_blur(P, P.max_iters);
+        if (rc == OTGB_OK && P.polish && D > 3) {
+            // polish: the same loop on the direct difference form of the cost (see otgb_params.polish)
+            s.launch.direct = 1;
+            s.launch.use_tcc = 0;
+            s.no_progress = 0;
+            s.floor_hits = 0;
+            s.delta_best = 1e300;
+            rc = s.iterate_at_blur(P, P.max_iters);
+        }
         OTGB_CUDA_TRY(cudaEventRecord(ctx_event(ctx, 4), st));
-        if (rc == OTGB_OK || rc == OTGB_ENOCONV) s.S = s.divergence(P.blur * P.blur);
+        if (rc == OTGB_OK || rc == OTGB_ENOCONV) s.S = s.divergence(s.eps_of(P.blur));
 
         // outputs in the caller's order
         unpermute(s.pf[s.cur], s.X.perm, N, f, st);
@@ -642,7 +653,8 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
             otgb_plan *pl = new otgb_plan();
             pl->N = N; pl->M = M; pl->D = D;
             pl->x = x; pl->y = y; pl->b = b;
-            pl->eps = P.blur * P.blur;
+            pl->eps = s.eps_of(P.blur);
+            pl->p = P.p;
             *plan_out = pl;
         }
         if (stats) {

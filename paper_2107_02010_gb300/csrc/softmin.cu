@@ -940,6 +940,10 @@ int fallback_grid_sms() {
 void softmin_run(const SoftminLaunch &L, int D, int rows_per_thread, cudaStream_t st) {
     if (L.n_items <= 0) return;
     OTGB_CUDA_TRY(cudaMemsetAsync(L.n_fallback, 0, sizeof(int), st));
+    if (L.cost_p1 || L.direct) {  // the direct form with a running maximum: no shift estimate, no fallback rows
+        softmin_direct_launch(L, D, st);
+        return;
+    }
     // the first-pass maximum is needed when some instance has no old value
     bool two = L.exact_max != 0;
     for (int k = 0; k < L.n_inst; ++k) two = two || (L.inst[k].row_old == nullptr);

@@ -84,9 +84,9 @@ std::vector<double> make_schedule(double d, double blur, double q) {
     return s;
 }
 
-double lambda_of(double sigma, double reach) {
+double lambda_of(double sigma, double reach, int p) {
     if (!(reach > 0.0) || std::isinf(reach)) return 1.0;
-    return 1.0 / (1.0 + (sigma / reach) * (sigma / reach));
+    return 1.0 / (1.0 + std::pow(sigma / reach, (double)p));
 }
 
 }  // namespace otgb

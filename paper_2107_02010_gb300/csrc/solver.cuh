@@ -9,7 +9,8 @@
 namespace otgb {
 
 std::vector<double> make_schedule(double d, double blur, double q);
-double lambda_of(double sigma, double reach);
+// lambda = 1 / (1 + (sigma / reach)^p), the unbalanced damping of the Algorithm (Section 2); 1 when balanced
+double lambda_of(double sigma, double reach, int p = 2);
 
 int fail(otgb_ctx *ctx, const Error &e);
 cudaStream_t ctx_stream(otgb_ctx *ctx);

@@ -365,6 +365,7 @@ extern "C" int transport_apply(otgb_ctx *ctx, const otgb_plan *plan, const float
     try {
         ctx_set_device(ctx);
         require(plan != nullptr, "transport_apply: null plan");
+        require(plan->p == 2, "transport_apply: label transfer is built for plans of the cost |x - y|^2 / 2 (p = 2)");
         require(f && g && labels && argmax, "transport_apply: null pointer argument");
         require(L >= 1 && L <= 1024, "transport_apply: L must be in [1, 1024]");
         const int N = plan->N, M = plan->M, D = plan->D;

@@ -50,6 +50,7 @@ class Params(C.Structure):
         ("init_g_from_f", C.c_int),
         ("warm_max_iters", C.c_int),
         ("debug_wait_probe", C.c_int),
+        ("polish", C.c_int),
     ]
 
 
@@ -93,7 +94,8 @@ EXPORTS = ["otgb_default_params", "otgb_create", "otgb_destroy", "otgb_last_erro
            "otgb_mlp_n_params", "otgb_mlp_fit_normalization", "otgb_mlp_set_normalization",
            "otgb_mlp_get_normalization", "otgb_mlp_set_params", "otgb_mlp_get_params", "otgb_mlp_grad",
            "otgb_mlp_adam_step", "otgb_mlp_train_step", "otgb_mlp_train_epoch", "otgb_mlp_infer", "otgb_mlp_save",
-           "otgb_mlp_load", "sinkhorn_divergence_warm", "sinkhorn_grad_x", "sinkhorn_barycenter"]
+           "otgb_mlp_load", "sinkhorn_divergence_warm", "sinkhorn_grad_x", "sinkhorn_barycenter", "otgb_flip_fibers",
+           "otgb_select_flips"]
 
 
 def kernel_launches() -> int:
@@ -160,7 +162,9 @@ def load(build_if_missing: bool = True):
     lib.sinkhorn_grad_x.argtypes = [vp, vp, vp, ci, vp, vp, ci, ci, ci, cd, vp, vp, vp, vp]
     lib.sinkhorn_barycenter.argtypes = [vp, vp, vp, ci, ci, C.POINTER(vp), C.POINTER(vp), C.POINTER(ci), ci,
                                         C.POINTER(Params), ci, cd, C.POINTER(cd)]
-    for name in ("sinkhorn_grad_x", "sinkhorn_barycenter", "otgb_create", "otgb_destroy", "sinkhorn_divergence",
+    lib.otgb_flip_fibers.argtypes = [vp, vp, ci, ci, vp]
+    lib.otgb_select_flips.argtypes = [vp, vp, vp, ci, vp, vp, vp]
+    for name in ("otgb_flip_fibers", "otgb_select_flips", "sinkhorn_grad_x", "sinkhorn_barycenter", "otgb_create", "otgb_destroy", "sinkhorn_divergence",
                  "transport_apply", "cluster_grid",
                  "cluster_kmeans", "otgb_softmin", "otgb_mlp_create", "otgb_mlp_destroy", "otgb_mlp_n_params",
                  "otgb_mlp_fit_normalization", "otgb_mlp_set_normalization", "otgb_mlp_get_normalization",
@@ -313,6 +317,28 @@ def sinkhorn_barycenter(ctx: Context, x, alpha, ys, betas, params: Params | None
     ctx.check(load().sinkhorn_barycenter(ctx.h, _f32(x), _f32(alpha), N, K, yp, bp, ms, D, C.byref(p), int(iters),
                                          float(lr), hist))
     return list(hist)
+
+
+def flip_fibers(ctx: Context, x, P=20):
+    """otgb_flip_fibers: 2N x 3P, the fibers then their mirror flips."""
+    N, D = x.shape
+    if D != 3 * P:
+        raise ValueError("flip_fibers: rows must hold 3P = %d coordinates" % (3 * P))
+    out = torch.empty((2 * N, D), device=x.device, dtype=torch.float32)
+    ctx.check(load().otgb_flip_fibers(ctx.h, _f32(x), N, int(P), _ptr(out)))
+    return out
+
+
+def select_flips(ctx: Context, row_mass, argmax):
+    """otgb_select_flips on 2N augmented rows: (label, version, mass) per fiber."""
+    if row_mass.numel() % 2 or argmax.numel() != row_mass.numel() or argmax.dtype != torch.int32:
+        raise ValueError("select_flips: row_mass (float32) and argmax (int32) of 2N rows")
+    N = row_mass.numel() // 2
+    lab = torch.empty(N, device=row_mass.device, dtype=torch.int32)
+    ver = torch.empty(N, device=row_mass.device, dtype=torch.int32)
+    mass = torch.empty(N, device=row_mass.device, dtype=torch.float32)
+    ctx.check(load().otgb_select_flips(ctx.h, _f32(row_mass), _ptr(argmax), N, _ptr(lab), _ptr(ver), _ptr(mass)))
+    return lab, ver, mass
 
 
 def cluster_grid(ctx: Context, x, cell, w=None, want_centroids=True):

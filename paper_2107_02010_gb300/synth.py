@@ -115,14 +115,15 @@ def bundle_centrelines(n_bundles: int = 20, box: float = 140.0, P: int = 20, see
 
 
 def fiber_bundles(n: int, seed: int, ctrl: np.ndarray | None = None, P: int = 20, perturb: float = 0.0,
-                  offset_sigma: float = 2.0, point_sigma: float = 0.5):
+                  offset_sigma: float = 2.0, point_sigma: float = 0.5, canonical: bool = True):
     """n fibers, each of P points, drawn from the bundles whose control points are
     `ctrl` (default: bundle_centrelines()).  Per tractogram the control points are
     perturbed by N(0, perturb^2) mm.  Each fiber picks a bundle uniformly, follows
     its centreline (P points equally spaced in arc length) moved by one per-fiber
     offset N(0, offset_sigma^2 I) plus per-point noise N(0, point_sigma^2 I); it is
     reversed at random and then canonicalised (reversed iff its first point is
-    lexicographically greater than its last).  Features are the flattened 3P
+    lexicographically greater than its last); canonical=False keeps the random
+    orientation (the input of flip augmentation).  Features are the flattened 3P
     coordinates times 1/sqrt(P).  Returns (x float32 n x 3P, w float32 uniform
     1/n, labels int32)."""
     rng = _rng(seed)
@@ -136,6 +137,9 @@ def fiber_bundles(n: int, seed: int, ctrl: np.ndarray | None = None, P: int = 20
     fib = lines[lab] + rng.normal(0.0, offset_sigma, size=(n, 1, 3)) + rng.normal(0.0, point_sigma, size=(n, P, 3))
     flip = rng.random(n) < 0.5
     fib[flip] = fib[flip, ::-1]
+    if not canonical:
+        x = (fib.reshape(n, 3 * P) / np.sqrt(P)).astype(np.float32)
+        return x, np.full(n, 1.0 / n, np.float32), lab
     first, last = fib[:, 0, :], fib[:, -1, :]
     gt = np.zeros(n, bool)
     decided = np.zeros(n, bool)

@@ -7,7 +7,14 @@ generator) is the reference.  The float32 paths -- dense single scale and the
 coarse-to-fine solve with k-means clusters, kernel truncation and
 extrapolation -- must reach S and all four duals within 1e-5 (Section 2: the
 accelerations change the path to the fixed point, not the fixed point); the
-reduced-precision tensor-core form within 1e-3."""
+reduced-precision tensor-core form within 1e-3.
+
+The coarse-to-fine solve reaches 1e-5 with params.polish = 1: the fast
+dot-product form leaves the duals a few 1e-5 away along the slowly
+contracting bundle translations of this unbalanced problem (S is exact to
+~1e-8 either way), and the polish repeats the loop at blur in the direct
+difference form of the cost.  The fast form's own dual error is measured and
+bounded here too."""
 import os
 
 import numpy as np
@@ -60,16 +67,29 @@ def test_fixture_is_the_stated_problem(case):
     assert float(ref["delta"]) < 1e-12
 
 
-@pytest.mark.parametrize("form", ["dense", "kmeans"])
+@pytest.mark.parametrize("form", ["dense", "kmeans", "kmeans-tc"])
 def test_fp32_fibers_match_converged_oracle(case, form):
-    kw = dict(precision=2)
-    if form == "kmeans":
-        kw.update(multiscale=1, cluster=1, k_clusters=40, kmeans_iters=10)
+    kw = dict(precision=2, polish=1)
+    if form.startswith("kmeans"):
+        kw.update(multiscale=1, cluster=1, k_clusters=40, kmeans_iters=10, check_every=3)
+    if form == "kmeans-tc":  # the tensor-core solve, polished on the CUDA cores
+        kw.update(precision=1)
     out = _solve(case, **kw)
     e = _errors(out, case["ref"])
     print("\n%s float32: %s, %d steps" % (form, {k: "%.2e" % v for k, v in e.items()}, out["stats"]["iters_total"]))
     for k, v in e.items():
         assert v < 1e-5, (form, k, v)
+
+
+def test_fast_forms_without_polish(case):
+    # without the polish: S to 1e-7, the duals to the measured few 1e-5
+    for prec in (2, 0):
+        out = _solve(case, precision=prec, multiscale=1, cluster=1, k_clusters=40, kmeans_iters=10, check_every=3)
+        e = _errors(out, case["ref"])
+        print("\nprecision %d, no polish: %s" % (prec, {k: "%.2e" % v for k, v in e.items()}))
+        assert e["S"] < 1e-7
+        for k in ("f", "g", "a", "b"):
+            assert e[k] < 1e-4, (k, e[k])
 
 
 def test_tensor_core_fibers_within_reduced_precision_bar(case):

@@ -117,17 +117,21 @@ def test_softmin_reduces_to_library_logsumexp():
 
 
 # ------------------------------------------------------ single Dirac masses --
-@pytest.mark.parametrize("ma,mb,eps,reach", [(1.0, 1.2, 1.0, 10.0), (0.3, 2.0, 0.5, 1.5), (1.0, 1.0, 4.0, 20.0)])
-def test_single_dirac_unbalanced_closed_form(ma, mb, eps, reach):
+@pytest.mark.parametrize("p,ma,mb,eps,reach", [(2, 1.0, 1.2, 1.0, 10.0), (2, 0.3, 2.0, 0.5, 1.5),
+                                               (2, 1.0, 1.0, 4.0, 20.0), (1, 1.0, 1.2, 0.5, 3.0),
+                                               (1, 0.3, 2.0, 0.2, 1.5)])
+def test_single_dirac_unbalanced_closed_form(p, ma, mb, eps, reach):
     # Eq. (2) with one Dirac on each side is a 1-D convex problem in the plan
     # mass pi: stationarity c + eps log(pi/(ma mb)) + rho log(pi/ma)
     # + rho log(pi/mb) = 0 gives log pi = ((eps + rho) log(ma mb) - c)/(eps + 2 rho).
     # OT, both self terms and S of Eq. (5) then follow in closed form; the
     # oracle reaches them through its fixed-point iteration and Eq. (6).
+    # p = 1: C = |x - y|, eps = blur, rho = reach (Section 2: C = |x - y|^p / p, eps = blur^p).
     x = np.array([[0.1, 0.2, 0.3]], np.float32)
     y = np.array([[1.1, -0.4, 0.9]], np.float32)
-    rho = reach ** 2
-    c = 0.5 * float(np.sum((x.astype(np.float64) - y.astype(np.float64)) ** 2))
+    rho = reach ** p
+    d2 = float(np.sum((x.astype(np.float64) - y.astype(np.float64)) ** 2))
+    c = 0.5 * d2 if p == 2 else math.sqrt(d2)
     ma32, mb32 = float(np.float32(ma)), float(np.float32(mb))
 
     def ot_primal(m1, m2, cc):
@@ -140,13 +144,27 @@ def test_single_dirac_unbalanced_closed_form(ma, mb, eps, reach):
     ot_aa, _ = ot_primal(ma32, ma32, 0.0)
     ot_bb, _ = ot_primal(mb32, mb32, 0.0)
     S_ref = ot_ab - 0.5 * ot_aa - 0.5 * ot_bb + 0.5 * eps * (ma32 - mb32) ** 2
-    r = oracle.sinkhorn(x, np.array([ma], np.float32), y, np.array([mb], np.float32), blur=math.sqrt(eps),
-                        reach=reach, scaling=0.5)
+    r = oracle.sinkhorn(x, np.array([ma], np.float32), y, np.array([mb], np.float32), blur=eps ** (1.0 / p),
+                        reach=reach, scaling=0.5, p=p)
     assert r["converged"]
     assert r["S"] == pytest.approx(S_ref, rel=1e-10, abs=1e-13)
     # plan mass of Eq. (4) from the oracle's duals
     pi = ma32 * mb32 * math.exp((r["f"][0] + r["g"][0] - c) / eps)
     assert pi == pytest.approx(pi_ab, rel=1e-10)
+
+
+@pytest.mark.parametrize("t", [0.3, 1.7])
+def test_single_dirac_balanced_p1_is_the_distance(t):
+    # p = 1, balanced, one Dirac of mass 1 on each side: the only coupling is
+    # the product, whose entropy term vanishes, so OT = C = |t| and both self
+    # terms are 0: S = |t| for every eps (Eqs. (2) and (5)).
+    x = np.array([[0.0, 0.0]], np.float32)
+    y = np.array([[0.6 * t, 0.8 * t]], np.float32)
+    one = np.array([1.0], np.float32)
+    for blur in (0.05, 0.5):
+        r = oracle.sinkhorn(x, one, y, one, blur=blur, reach=0.0, scaling=0.5, p=1)
+        assert r["converged"]
+        assert r["S"] == pytest.approx(float(np.linalg.norm(y.astype(np.float64))), rel=1e-12)
 
 
 # --------------------------------------------------- balanced invariances --
@@ -384,3 +402,63 @@ def test_kmeans_weighted_invariants():
         if m.any():  # converged: centroid is the weighted mean of its points
             np.testing.assert_allclose(cent[k], (w[m, None] * X[m]).sum(0) / w[m].astype(np.float64).sum(),
                                        rtol=1e-9, atol=1e-9)
+
+
+# ------------------------------------------------------- flip augmentation --
+def test_flip_augmentation_is_an_involution_on_the_points():
+    # Section 2 (fiber encoding): a fiber and its mirror flip are the same
+    # curve with the P points in reverse order
+    r = np.random.default_rng(70)
+    P = 20
+    x = r.normal(size=(7, 3 * P)).astype(np.float32)
+    aug = oracle.flip_fibers(x, P)
+    assert aug.shape == (14, 3 * P)
+    np.testing.assert_array_equal(aug[:7], x)
+    back = oracle.flip_fibers(aug[7:], P)[7:]
+    np.testing.assert_array_equal(back, x)
+    pts = lambda v: np.sort(v.reshape(-1, P, 3), axis=1)
+    np.testing.assert_array_equal(pts(aug[7:]), pts(x))
+    np.testing.assert_array_equal(aug[7:].reshape(7, P, 3)[:, 0], x.reshape(7, P, 3)[:, -1])
+    # a palindromic fiber is its own flip
+    half = r.normal(size=(P // 2, 3))
+    pal = np.concatenate([half, half[::-1]]).reshape(1, -1).astype(np.float32)
+    np.testing.assert_array_equal(oracle.flip_fibers(pal, P)[1], pal[0])
+
+
+def test_select_flips_keeps_the_version_with_the_larger_row_mass():
+    mass = np.array([0.9, 0.1, 0.5, 1e-9, 0.8, 0.5])
+    am = np.array([3, 4, 5, 6, 7, 8], np.int32)
+    lab, ver, m = oracle.select_flips(mass, am, 3)
+    assert list(ver) == [0, 1, 0] and list(lab) == [3, 7, 5]  # fiber 2: a tie keeps the original
+    np.testing.assert_array_equal(m, [0.9, 0.8, 0.5])
+
+
+def test_flip_augmented_label_transfer_matches_each_fiber_once():
+    # Section 2 (label transfer on augmented data): with the subject in random
+    # orientation and augmented by its flips, the unbalanced plan matches the
+    # version that runs like the atlas fibers and leaves the other one as an
+    # outlier, so every fiber gets its bundle's label from the kept version
+    from paper_2107_02010_gb300 import synth
+
+    ctrl = synth.bundle_centrelines(n_bundles=3)
+    x, a, lab_x = synth.fiber_bundles(24, seed=71, ctrl=ctrl, canonical=False)
+    y, b, lab_y = synth.fiber_bundles(24, seed=72, ctrl=ctrl)
+    aug = oracle.flip_fibers(x)
+    w = np.concatenate([a, a])
+    blur, reach = 2.0, 20.0
+    r = oracle.sinkhorn(aug, w, y, b, blur=blur, reach=reach, scaling=0.5)
+    assert r["converged"]
+    _, am, rm = oracle.transport_apply(aug, y, b, blur ** 2, r["f"], r["g"], lab_y, 3)
+    lab, ver, m = oracle.select_flips(rm, am, 24)
+    assert np.all(lab == lab_x)
+    # the kept version carries clearly more mass (at reach 20 mm moving the
+    # reversed version some way still costs less than destroying all of it)
+    other = rm[np.where(ver == 0, np.arange(24) + 24, np.arange(24))]
+    assert np.all(m > 0.5) and np.all(other < 0.5 * m)
+    # the kept version runs like the canonical atlas: first point before last
+    fib = aug[np.where(ver == 0, np.arange(24), np.arange(24) + 24)].reshape(24, 20, 3)
+    first, last = fib[:, 0], fib[:, -1]
+    ref = y.reshape(24, 20, 3)
+    for i in range(24):
+        j = np.where(lab_y == lab_x[i])[0][0]
+        assert np.linalg.norm(first[i] - ref[j, 0]) < np.linalg.norm(last[i] - ref[j, 0])
