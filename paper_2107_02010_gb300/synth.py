@@ -88,15 +88,22 @@ def density_maps(grid: int = 64, n_tubes: int = 30, tube_sigma: float = 1.5, n_k
     given total masses, the weights.  Returns (x, a, y, b) float32."""
     out = []
     for seed, mass in zip(seeds, masses):
-        rng = _rng(seed)
-        vox, dens = _density_volume(rng, grid, n_tubes, tube_sigma)
-        k = min(n_keep, int(np.count_nonzero(dens > 0)))
-        idx = np.argpartition(-dens, k - 1)[:k]
-        idx.sort()
-        w = dens[idx]
-        w = w / w.sum() * mass
-        out += [vox[idx].astype(np.float32), w.astype(np.float32)]
+        out += list(density_map(grid, n_tubes, tube_sigma, n_keep, seed, mass))
     return tuple(out)
+
+
+def density_map(grid: int = 64, n_tubes: int = 30, tube_sigma: float = 1.5, n_keep: int = 100_000, seed: int = 1,
+                mass: float = 1.0):
+    """One track-density volume of `density_maps` (same recipe, one seed).
+    Returns (points float32 n x 3, weights float32)."""
+    rng = _rng(seed)
+    vox, dens = _density_volume(rng, grid, n_tubes, tube_sigma)
+    k = min(n_keep, int(np.count_nonzero(dens > 0)))
+    idx = np.argpartition(-dens, k - 1)[:k]
+    idx.sort()
+    w = dens[idx]
+    w = w / w.sum() * mass
+    return vox[idx].astype(np.float32), w.astype(np.float32)
 
 
 def _resample_arclength(curve: np.ndarray, P: int) -> np.ndarray:
@@ -150,3 +157,54 @@ def fiber_bundles(n: int, seed: int, ctrl: np.ndarray | None = None, P: int = 20
     x = (fib.reshape(n, 3 * P) / np.sqrt(P)).astype(np.float32)
     w = np.full(n, 1.0 / n, np.float32)
     return x, w, lab
+
+
+def unit_mass(w: np.ndarray, bits: int = 30) -> np.ndarray:
+    """Positive weights of total mass exactly 1 in float32 and in double: each
+    weight a multiple of 2^-b (at least one unit), the units summing to 2^b
+    (largest remainders rounded up), b <= bits the finest resolution at which
+    every weight is exact in float32.  Balanced transport needs equal masses
+    on both sides, which float32 rounding of w / sum(w) breaks."""
+    w = np.asarray(w, np.float64)
+    # a multiple of 2^-b below 2^(24 - b) is exact in float32
+    wmax = w.max() / w.sum()
+    while bits > 1 and wmax * 2.0 >= 2.0 ** (24 - bits):
+        bits -= 1
+    units = 1 << bits
+    q = w / w.sum() * units
+    k = np.maximum(np.floor(q), 1).astype(np.int64)
+    rest = units - int(k.sum())
+    order = np.argsort(-(q - np.floor(q)), kind="stable")
+    if rest >= 0:
+        k[order[:rest]] += 1
+    else:  # too many rounded-up ones: take units back from the largest weights
+        big = np.argsort(-k, kind="stable")
+        k[big[:-rest]] -= 1
+    assert k.sum() == units and k.min() >= 1
+    out = (k / units).astype(np.float32)
+    assert np.all(out.astype(np.float64) * units == k)  # exact in float32
+    return out
+
+
+def barycenter_maps(K: int = 5, grid: int = 64, n_keep: int = 20_000, upsample: int = 6, seed: int = 40):
+    """Inputs of the track-density atlas (Section 2, "Track density atlas"; the
+    Results section uses 5 maps of ~20,000 voxels and a barycenter initialised
+    with their average density, up-sampled by a factor of 6): K maps from
+    `density_maps` (30 tubes each, seeds seed..seed+K-1) with unit mass, and
+    the initial barycenter: the union of their voxels weighted by the average
+    density, each voxel replaced by `upsample` points drawn uniformly inside it.
+    Returns (x0, a0, ys, bs); all weights have total mass exactly 1."""
+    ys, bs = [], []
+    for k in range(K):
+        y, b = density_map(grid=grid, n_keep=n_keep, seed=seed + k)
+        ys.append(y)
+        bs.append(unit_mass(b))
+    keys = np.concatenate([np.floor(y).astype(np.int64) @ np.array([grid * grid, grid, 1]) for y in ys])
+    wts = np.concatenate(bs).astype(np.float64) / K
+    uniq, inv = np.unique(keys, return_inverse=True)
+    dens = np.bincount(inv, weights=wts)
+    vox = np.stack([uniq // (grid * grid), (uniq // grid) % grid, uniq % grid], axis=1).astype(np.float64)
+    rng = _rng(seed + 2 * K)
+    x0 = (np.repeat(vox, upsample, axis=0) + rng.uniform(0.0, 1.0, size=(vox.shape[0] * upsample, 3)))
+    a0 = unit_mass(np.repeat(dens, upsample))
+    return x0.astype(np.float32), a0, ys, bs

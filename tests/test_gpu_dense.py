@@ -270,7 +270,7 @@ def test_invalid_arguments_are_rejected(ctx):
 
     x, a, y, b = synth.rotated_cloud(50, seed=1)
     X, A, Y, B = T(x), T(a), T(y), T(b)
-    for kw in (dict(p=1), dict(blur=0.0), dict(blur=-1.0), dict(scaling=1.0), dict(scaling=0.0)):
+    for kw in (dict(p=3), dict(blur=0.0), dict(blur=-1.0), dict(scaling=1.0), dict(scaling=0.0)):
         with pytest.raises(otgb.OtgbError) as e:
             otgb.sinkhorn_divergence(ctx, X, A, Y, B, otgb.default_params(**kw))
         assert e.value.code == -1

@@ -67,3 +67,25 @@ def test_fiber_bundles_layout_orientation_and_labels(P):
         assert spread < 4.0, (k, spread)
     x2, _, lab2 = synth.fiber_bundles(3000, seed=4, ctrl=ctrl, P=P, perturb=3.0)
     assert np.array_equal(x, x2) and np.array_equal(lab, lab2)
+
+
+def test_unit_mass_is_exact_in_float32():
+    r = np.random.default_rng(5)
+    for n in (1, 7, 1000, 300_000):
+        w = synth.unit_mass(r.uniform(0.1, 2.0, n))
+        assert w.dtype == np.float32 and np.all(w > 0)
+        assert w.astype(np.float64).sum() == 1.0
+
+
+def test_barycenter_maps_recipe():
+    # K unit-mass maps of n_keep voxels; the initial support is every voxel of
+    # the union, up-sampled, with the average density as weight
+    x0, a0, ys, bs = synth.barycenter_maps(K=3, grid=24, n_keep=400, upsample=4)
+    assert len(ys) == 3 and all(y.shape == (400, 3) for y in ys)
+    assert all(b.astype(np.float64).sum() == 1.0 for b in bs)
+    assert a0.astype(np.float64).sum() == 1.0
+    assert x0.shape[0] % 4 == 0
+    union = np.unique(np.concatenate([np.floor(y) for y in ys]), axis=0)
+    assert x0.shape[0] == 4 * union.shape[0]
+    cells = np.unique(np.floor(x0), axis=0)
+    np.testing.assert_array_equal(cells, union)
