@@ -21,6 +21,7 @@ Other workloads (not the default line; each prints its own JSON line):
     --workload density            track-density maps (two 64^3 volumes, ~100k voxels, D = 3, grid clusters)
     --workload mlp [--n N]        warm-start network: inference and training throughput
     --workload barycenter         track-density atlas: free-support barycenter of 5 maps
+    --workload rates              measured per-clock rates of MUFU ex2 and FP32 FMA (roofline constants)
 """
 from __future__ import annotations
 
@@ -319,6 +320,13 @@ def run_fibers(args):
         clocks_tc = stop_clock_sampler(sampler, sf, local)
         tc = summarize(mstc, outstc)
         tc["clocks"] = clocks_tc
+        # the paper's own schedule, q = 0.9 on sigma (Section 2), against the workload's q = 0.5:
+        # tensor-core form, one untimed and three timed solves
+        pq = fiber_params(otgb, n, 1, args.tol, args.max_iters)
+        pq.scaling = 0.9
+        msq, outsq = timed_solves(lambda: otgb.sinkhorn_divergence(ctx, X, A, Y, B, pq, raise_on_noconv=False),
+                                  3, 1, l2, st)
+        tc["q_0.9"] = summarize(msq, outsq)
 
     # S* of the stopping-rule check: one tightly converged float32 solve (untimed)
     # (at least 60 steps at blur, past the point where the float32 iteration stops contracting)
@@ -376,6 +384,7 @@ def run_fibers(args):
         peak_tc = min(pk.get("bf16_tflops", 1910.7) * 1e12 / TC60_TENSOR_FLOP_PER_PAIR,
                       SFU_EX2_PER_CLK_SM * n_sm * clk * 1e6)
         ach_tc = tc["pairs_per_solve"] / (tc["softmin_ms_per_solve"] / 1e3)
+        tc["q_0.9"]["rel_err_S"] = abs(tc["q_0.9"]["S"] - S_star) / abs(S_star)
         tc.update({"dtype": "bf16 hi/lo cross term (three products), f32 accumulate, f32 log-sum-exp",
                    "rel_err_S": abs(tc["S"] - S_star) / abs(S_star),
                    "speedup_vs_fp32": s32["time_to_solve_ms"] / tc["time_to_solve_ms"],
@@ -471,6 +480,23 @@ def run_density(args):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+# ------------------------------------------------------------------- rates --
+def run_rates(args):
+    """Measured per-SM, per-clock unit rates (otgb_unit_rates): MUFU ex2,
+    scalar FP32 FMA, packed FP32x2 FMA -- the constants of the ALU rooflines."""
+    import torch
+    from paper_2107_02010_gb300 import otgb
+
+    ctx = otgb.Context()
+    vals = [otgb.unit_rates(ctx) for _ in range(max(1, args.steps))]
+    med = {k: statistics.median(v[k] for v in vals) for k in vals[0]}
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    print(json.dumps({"metric": "unit rates", "workload": "rates", "unit": "lane operations per clock per SM",
+                      "ex2": med["ex2"], "fma": med["fma"], "fma2": med["fma2"], "repeats": len(vals),
+                      "n_sm": n_sm, "used_by_roofline": {"ex2": SFU_EX2_PER_CLK_SM, "fma": FP32_LANES_PER_CLK_SM}}))
     return 0
 
 
@@ -614,7 +640,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fibers", choices=["fibers", "density", "mlp", "barycenter"])
+    ap.add_argument("--workload", default="fibers", choices=["fibers", "density", "mlp", "barycenter", "rates"])
     ap.add_argument("--iters", type=int, default=5, help="barycenter: gradient steps")
     ap.add_argument("--n", type=int, default=0, help="fibers: points per side (1,000,000); mlp: rows (1,048,576)")
     ap.add_argument("--grid", type=int, default=64)
@@ -640,6 +666,8 @@ def main():
         return run_mlp(args)
     if args.workload == "barycenter":
         return run_barycenter(args)
+    if args.workload == "rates":
+        return run_rates(args)
     return run_fibers(args)
 
 

@@ -421,6 +421,16 @@ int sinkhorn_divergence_warm(otgb_ctx *ctx, otgb_mlp *mlp, const float *x, const
                              double *cost_host, float *f, float *g, float *a_self, float *b_self,
                              otgb_plan **plan_out, otgb_stats *stats);
 
+/*
+ * Measured per-SM, per-clock throughput of the units that bound the softmin
+ * kernels (the denominators of their rooflines; the paper has no counterpart):
+ * lane operations per clock per SM of MUFU ex2 (ex2.approx.ftz.f32), scalar
+ * FP32 FMA and packed FP32x2 FMA (two lane operations each), from short
+ * dependency-chain kernels timed with the SM cycle counter on the context's
+ * device.  All three outputs are host doubles.
+ */
+int otgb_unit_rates(otgb_ctx *ctx, double *ex2_per_clk_sm, double *fma_per_clk_sm, double *fma2_per_clk_sm);
+
 /* Number of CUDA kernels this library has launched in this process (all
    contexts), for accounting by benchmarks. */
 unsigned long long otgb_kernel_launches(void);

@@ -217,11 +217,19 @@ extern "C" int sinkhorn_barycenter(otgb_ctx *ctx, float *x, const float *alpha, 
         Workspace &ws = ctx_ws(ctx);
         int Mmax = 0;
         for (int k = 0; k < K; ++k) Mmax = std::max(Mmax, Ms[k]);
-        // buffers that survive the solves' own workspace use: named apart
-        float *f = ws.get<float>("bary:f", N);
-        float *a = ws.get<float>("bary:a", N);
-        float *g = ws.get<float>("bary:g", Mmax);
+        // buffers that survive the solves' own workspace use: named apart.  The four duals of each
+        // measure are kept from one step to the next: the points move little per step, so after the
+        // first step every solve starts at blur from the duals of the previous one (the fixed point
+        // decides the result, the start only its cost).
         float *G = ws.get<float>("bary:G", (size_t)N * D);
+        std::vector<float *> fk(K), gk(K), ak(K), bk(K);
+        for (int k = 0; k < K; ++k) {
+            const std::string s = std::to_string(k);
+            fk[k] = ws.get<float>("bary:f" + s, N);
+            ak[k] = ws.get<float>("bary:a" + s, N);
+            gk[k] = ws.get<float>("bary:g" + s, Ms[k]);
+            bk[k] = ws.get<float>("bary:b" + s, Ms[k]);
+        }
         const double eps = P.p == 1 ? P.blur : P.blur * P.blur;
         for (int it = 0; it <= iters; ++it) {
             double Ssum = 0.0;
@@ -229,8 +237,17 @@ extern "C" int sinkhorn_barycenter(otgb_ctx *ctx, float *x, const float *alpha, 
             if (last && !S_hist) break;
             for (int k = 0; k < K; ++k) {
                 double S = 0.0;
-                const int rc = sinkhorn_divergence(ctx, x, alpha, N, ys[k], betas[k], Ms[k], D, &P, &S, f, g, a,
-                                                   nullptr, nullptr, nullptr);
+                otgb_params Pk = P;
+                if (it > 0) {
+                    Pk.f_init = fk[k];
+                    Pk.g_init = gk[k];
+                    Pk.a_init = ak[k];
+                    Pk.b_init = bk[k];
+                    Pk.sigma_start = P.blur;
+                }
+                float *f = fk[k], *g = gk[k], *a = ak[k];
+                const int rc = sinkhorn_divergence(ctx, x, alpha, N, ys[k], betas[k], Ms[k], D, &Pk, &S, f, g, a,
+                                                   bk[k], nullptr, nullptr);
                 if (rc != OTGB_OK && rc != OTGB_ENOCONV) return rc;  // the message is already set
                 Ssum += S;
                 if (!last)

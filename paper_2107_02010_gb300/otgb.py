@@ -95,7 +95,7 @@ EXPORTS = ["otgb_default_params", "otgb_create", "otgb_destroy", "otgb_last_erro
            "otgb_mlp_get_normalization", "otgb_mlp_set_params", "otgb_mlp_get_params", "otgb_mlp_grad",
            "otgb_mlp_adam_step", "otgb_mlp_train_step", "otgb_mlp_train_epoch", "otgb_mlp_infer", "otgb_mlp_save",
            "otgb_mlp_load", "sinkhorn_divergence_warm", "sinkhorn_grad_x", "sinkhorn_barycenter", "otgb_flip_fibers",
-           "otgb_select_flips"]
+           "otgb_select_flips", "otgb_unit_rates"]
 
 
 def kernel_launches() -> int:
@@ -163,6 +163,8 @@ def load(build_if_missing: bool = True):
     lib.sinkhorn_barycenter.argtypes = [vp, vp, vp, ci, ci, C.POINTER(vp), C.POINTER(vp), C.POINTER(ci), ci,
                                         C.POINTER(Params), ci, cd, C.POINTER(cd)]
     lib.otgb_flip_fibers.argtypes = [vp, vp, ci, ci, vp]
+    lib.otgb_unit_rates.argtypes = [vp, C.POINTER(cd), C.POINTER(cd), C.POINTER(cd)]
+    lib.otgb_unit_rates.restype = ci
     lib.otgb_select_flips.argtypes = [vp, vp, vp, ci, vp, vp, vp]
     for name in ("otgb_flip_fibers", "otgb_select_flips", "sinkhorn_grad_x", "sinkhorn_barycenter", "otgb_create", "otgb_destroy", "sinkhorn_divergence",
                  "transport_apply", "cluster_grid",
@@ -317,6 +319,14 @@ def sinkhorn_barycenter(ctx: Context, x, alpha, ys, betas, params: Params | None
     ctx.check(load().sinkhorn_barycenter(ctx.h, _f32(x), _f32(alpha), N, K, yp, bp, ms, D, C.byref(p), int(iters),
                                          float(lr), hist))
     return list(hist)
+
+
+def unit_rates(ctx: Context):
+    """otgb_unit_rates: measured lane operations per clock per SM of MUFU ex2,
+    scalar FP32 FMA and packed FP32x2 FMA."""
+    e, f, f2 = C.c_double(), C.c_double(), C.c_double()
+    ctx.check(load().otgb_unit_rates(ctx.h, C.byref(e), C.byref(f), C.byref(f2)))
+    return {"ex2": e.value, "fma": f.value, "fma2": f2.value}
 
 
 def flip_fibers(ctx: Context, x, P=20):

@@ -92,6 +92,41 @@ def test_fast_forms_without_polish(case):
             assert e[k] < 1e-4, (k, e[k])
 
 
+def test_warm_started_solve_matches_converged_oracle(case):
+    # the learned warm start (a network trained on the f of plain solves of
+    # other subjects against the same atlas) only changes where the loop
+    # starts: the warm solve of the fixture's subject reaches the oracle's
+    # fixed point (polished, as above)
+    otgb, ctx = case["otgb"], case["ctx"]
+    ctrl = synth.bundle_centrelines()
+    common = dict(blur=BLUR, reach=REACH, scaling=0.5, multiscale=1, cluster=1, k_clusters=40, kmeans_iters=10,
+                  check_every=3, max_iters=20000)
+    X, F, b_atlas = [], [], None
+    for s in range(12):
+        x, a, _ = synth.fiber_bundles(2000, seed=200 + s, ctrl=ctrl, perturb=3.0)
+        xt, at = torch.from_numpy(x).cuda(), torch.from_numpy(a).cuda()
+        r = otgb.sinkhorn_divergence(ctx, xt, at, case["Y"], case["B"], otgb.default_params(tol=1e-8, **common),
+                                     want_self=True)
+        X.append(xt)
+        F.append(r["f"])
+        if b_atlas is None:
+            b_atlas = r["b_self"].clone()
+    Xc, Fc = torch.cat(X), torch.cat(F)
+    net = otgb.Mlp(ctx, 60, 256, seed=3)
+    net.fit_normalization(Xc, Fc)
+    for e in range(40):
+        net.train_epoch(Xc, Fc, 2048, 1e-5 + 0.5 * (1e-3 - 1e-5) * (1 + np.cos(np.pi * e / 40)), seed=e)
+    p = otgb.default_params(tol=1e-9, polish=1, **common)
+    out = otgb.sinkhorn_divergence_warm(ctx, net, case["X"], case["A"], case["Y"], case["B"], p, b_atlas=b_atlas,
+                                        want_self=True)
+    assert out["stats"]["warm_start"] in (1, 2)
+    e = _errors(out, case["ref"])
+    print("\nwarm start (%s): %s, %d steps" % ("warm" if out["stats"]["warm_start"] == 1 else "fell back",
+                                               {k: "%.2e" % v for k, v in e.items()}, out["stats"]["iters_total"]))
+    for k, v in e.items():
+        assert v < 1e-5, (k, v)
+
+
 def test_tensor_core_fibers_within_reduced_precision_bar(case):
     out = _solve(case, precision=1, multiscale=1, cluster=1, k_clusters=40, kmeans_iters=10)
     e = _errors(out, case["ref"])
