@@ -131,9 +131,9 @@ struct ListLaunch {
     ListInst inst[4];
     int base[5];            // flat index of (inst, 0)
     int nwords;
-    int *counts;            // per flat block
-    const int *col_ptr;     // per flat block (write pass)
-    int *list;
+    int *counts;            // count pass, per flat block: kept columns, kept clusters (2 ints)
+    const int *rng_ptr;     // write pass, per flat block: first range entry
+    int2 *rng;              // write pass: (first column, position) per kept cluster, then the sentinel
 };
 
 __device__ __forceinline__ void flat_to_inst(const ListLaunch &L, int f, int &k, int &b) {
@@ -142,11 +142,12 @@ __device__ __forceinline__ void flat_to_inst(const ListLaunch &L, int f, int &k,
     b = f - L.base[k];
 }
 
-// Union of the keep bits of a block's row clusters; each thread owns a
-// contiguous range of words so that the column list comes out in increasing
-// order.  WRITE = false: count the kept columns; true: write them.
-constexpr int kListSmem = 4096;
-
+// Kept columns of a block: the union of the keep bits of its row clusters.
+// The columns are sorted by cluster, so every kept cluster J is one range of
+// consecutive columns [off_c[J], off_c[J+1]).  Each thread owns a contiguous
+// range of bit words, so the ranges come out in increasing order.
+// WRITE = false: count the kept columns and clusters; true: write the ranges
+// with their positions (exclusive scans over the threads), then the sentinel.
 template <bool WRITE>
 __global__ void list_kernel(const __grid_constant__ ListLaunch L) {
     __shared__ int scan[256], sscan2[256];
@@ -156,40 +157,18 @@ __global__ void list_kernel(const __grid_constant__ ListLaunch L) {
     const int cl0 = P.blk_cl[2 * b], cl1 = P.blk_cl[2 * b + 1];
     const int wpt = (L.nwords + blockDim.x - 1) / blockDim.x;
     const int w0 = threadIdx.x * wpt, w1 = min(L.nwords, w0 + wpt);
-    int cnt = 0;
+    int cnt = 0, nq = 0;
     for (int w = w0; w < w1; ++w) {
         unsigned u = 0;
         for (int I = cl0; I < cl1; ++I) u |= P.bits[(size_t)I * L.nwords + w];
+        nq += __popc(u);
         while (u) {
             const int J = w * 32 + __ffs(u) - 1;
             u &= u - 1;
             cnt += P.off_c[J + 1] - P.off_c[J];
         }
     }
-    if (!WRITE) {
-        scan[threadIdx.x] = cnt;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) scan[threadIdx.x] += scan[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) L.counts[blockIdx.x] = scan[0];
-        return;
-    }
-    // Kept clusters of this block in order, with the list position where each
-    // one's columns start, go to shared memory; then the CTA writes the list
-    // with consecutive threads on consecutive positions (each position finds
-    // its cluster by binary search).  Blocks that keep more clusters than fit
-    // write per thread.
-    __shared__ int sJ[kListSmem], sP[kListSmem + 1];
-    __shared__ int nq_tot;
-    int nq = 0;
-    for (int w = w0; w < w1; ++w) {
-        unsigned u = 0;
-        for (int I = cl0; I < cl1; ++I) u |= P.bits[(size_t)I * L.nwords + w];
-        nq += __popc(u);
-    }
-    // exclusive scans of the per-thread column and cluster counts
+    // inclusive scans of the per-thread column and cluster counts
     scan[threadIdx.x] = cnt;
     sscan2[threadIdx.x] = nq;
     __syncthreads();
@@ -201,46 +180,39 @@ __global__ void list_kernel(const __grid_constant__ ListLaunch L) {
         sscan2[threadIdx.x] += v2;
         __syncthreads();
     }
-    const int base = L.col_ptr[blockIdx.x];
-    int pos = scan[threadIdx.x] - cnt;
-    if (threadIdx.x == blockDim.x - 1) nq_tot = sscan2[threadIdx.x];
-    __syncthreads();
-    const int Q = nq_tot, T = scan[blockDim.x - 1];
-    if (Q > kListSmem) {
-        for (int w = w0; w < w1; ++w) {
-            unsigned u = 0;
-            for (int I = cl0; I < cl1; ++I) u |= P.bits[(size_t)I * L.nwords + w];
-            while (u) {
-                const int J = w * 32 + __ffs(u) - 1;
-                u &= u - 1;
-                for (int j = P.off_c[J]; j < P.off_c[J + 1]; ++j) L.list[base + pos++] = j;
-            }
+    const int T = scan[blockDim.x - 1], Q = sscan2[blockDim.x - 1];
+    if (!WRITE) {
+        if (threadIdx.x == 0) {
+            L.counts[2 * blockIdx.x] = T;
+            L.counts[2 * blockIdx.x + 1] = Q;
         }
         return;
     }
-    int q = sscan2[threadIdx.x] - nq;
+    int2 *out = L.rng + L.rng_ptr[blockIdx.x];
+    int pos = scan[threadIdx.x] - cnt, q = sscan2[threadIdx.x] - nq;
     for (int w = w0; w < w1; ++w) {
         unsigned u = 0;
         for (int I = cl0; I < cl1; ++I) u |= P.bits[(size_t)I * L.nwords + w];
         while (u) {
             const int J = w * 32 + __ffs(u) - 1;
             u &= u - 1;
-            sJ[q] = J;
-            sP[q] = pos;
+            out[q++] = make_int2(P.off_c[J], pos);
             pos += P.off_c[J + 1] - P.off_c[J];
-            ++q;
         }
     }
-    if (threadIdx.x == 0) sP[Q] = T;
-    __syncthreads();
-    for (int p = threadIdx.x; p < T; p += blockDim.x) {
-        int lo = 0, hi = Q - 1;  // the last q with sP[q] <= p
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sP[mid] <= p) lo = mid;
-            else hi = mid - 1;
-        }
-        L.list[base + p] = P.off_c[sJ[lo]] + (p - sP[lo]);
+    if (threadIdx.x == blockDim.x - 1) out[Q] = make_int2(0, T);
+}
+
+// One CTA per flat block: the block's ranges written out as one column index
+// per position (list[list_ptr[b] + pos]).
+__global__ void expand_kernel(const int *rng_ptr, const int2 *rng, const int *list_ptr, int *list) {
+    const int b = blockIdx.x;
+    const int k0 = rng_ptr[b], k1 = rng_ptr[b + 1] - 1;  // k1: the sentinel
+    int *out = list + list_ptr[b];
+    for (int k = k0; k < k1; ++k) {
+        const int2 e = rng[k];
+        const int len = rng[k + 1].y - e.y;
+        for (int i = threadIdx.x; i < len; i += blockDim.x) out[e.y + i] = e.x + i;
     }
 }
 
@@ -437,8 +409,10 @@ int Multiscale::run_schedule(Solver &s, const otgb_params &P, const std::vector<
             I.row_out = outp[q];
             I.lam = lam;
             I.omega = 1.0f;
+            I.col_rng = nullptr;
+            I.rng_ptr = nullptr;
             I.col_list = nullptr;
-            I.col_ptr = nullptr;
+            I.list_ptr = nullptr;
         }
         std::vector<int4> items;
         for (int q = 0; q < 4; ++q) {
@@ -530,27 +504,49 @@ void Multiscale::before_fine_step(Solver &s, double sigma) {
     }
     LL.nwords = nwords;
     const int nflat = LL.base[4];
-    LL.counts = ws.get<int>("ms:cnt", nflat);
+    LL.counts = ws.get<int>("ms:cnt", 2 * (size_t)nflat);
     list_kernel<false><<<nflat, 256, 0, st>>>(LL);
     OTGB_CHECK_LAUNCH();
-    std::vector<int> cnt(nflat), ptr(nflat + 1);
-    OTGB_CUDA_TRY(cudaMemcpyAsync(cnt.data(), LL.counts, sizeof(int) * nflat, cudaMemcpyDeviceToHost, st));
+    std::vector<int> cq(2 * (size_t)nflat), cnt(nflat), ptr(nflat + 1);
+    OTGB_CUDA_TRY(cudaMemcpyAsync(cq.data(), LL.counts, sizeof(int) * 2 * nflat, cudaMemcpyDeviceToHost, st));
     OTGB_CUDA_TRY(cudaStreamSynchronize(st));
+    // range entries per block: its kept clusters and a sentinel; kRngPad padding entries after the
+    // last block keep every entry the walk reads past a sentinel readable
     ptr[0] = 0;
-    for (int f = 0; f < nflat; ++f) ptr[f + 1] = ptr[f] + cnt[f];
-    int *d_ptr = ws.get<int>("ms:colptr", nflat + 1);
+    for (int f = 0; f < nflat; ++f) {
+        cnt[f] = cq[2 * f];
+        ptr[f + 1] = ptr[f] + cq[2 * f + 1] + 1;
+    }
+    int *d_ptr = ws.get<int>("ms:rngptr", nflat + 1);
     OTGB_CUDA_TRY(cudaMemcpyAsync(d_ptr, ptr.data(), sizeof(int) * (nflat + 1), cudaMemcpyHostToDevice, st));
-    int *d_list = ws.get<int>("ms:list", (size_t)std::max(ptr[nflat], 1));
-    LL.col_ptr = d_ptr;
-    LL.list = d_list;
+    int2 *d_rng = ws.get<int2>("ms:rng", (size_t)ptr[nflat] + kRngPad);
+    OTGB_CUDA_TRY(cudaMemsetAsync(d_rng + ptr[nflat], 0, sizeof(int2) * kRngPad, st));
+    LL.rng_ptr = d_ptr;
+    LL.rng = d_rng;
     list_kernel<true><<<nflat, 256, 0, st>>>(LL);
     OTGB_CHECK_LAUNCH();
-    // instances walk the lists; work items split long lists
+    // D <= 3 (grid cells of a few dozen points, i.e. short ranges): the ranges are also expanded into
+    // one column index per position, which the kernels read instead of walking short ranges
+    int *d_lptr = nullptr, *d_list = nullptr;
+    if (D <= 3) {
+        std::vector<int> lp(nflat + 1);
+        lp[0] = 0;
+        for (int f = 0; f < nflat; ++f) lp[f + 1] = lp[f] + cnt[f];
+        d_lptr = ws.get<int>("ms:listptr", nflat + 1);
+        OTGB_CUDA_TRY(cudaMemcpyAsync(d_lptr, lp.data(), sizeof(int) * (nflat + 1), cudaMemcpyHostToDevice, st));
+        d_list = ws.get<int>("ms:list", (size_t)std::max(lp[nflat], 1));
+        expand_kernel<<<nflat, 256, 0, st>>>(d_ptr, d_rng, d_lptr, d_list);
+        OTGB_CHECK_LAUNCH();
+        OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // lp goes out of scope
+    }
+    // instances walk the ranges (or read the lists); work items split long sequences of kept columns
     std::vector<std::vector<int>> ncols(4);
     double kept = 0.0, dense = 0.0;
     for (int q = 0; q < 4; ++q) {
         SoftminInst &I = s.launch.inst[q];
-        I.col_ptr = d_ptr + LL.base[q];
+        I.rng_ptr = d_ptr + LL.base[q];
+        I.col_rng = d_rng;
+        I.list_ptr = d_lptr ? d_lptr + LL.base[q] : nullptr;
         I.col_list = d_list;
         ncols[q].assign(cnt.begin() + LL.base[q], cnt.begin() + LL.base[q + 1]);
         const std::vector<int> &hb = (q == 0 || q == 3) ? hbx : hby;

@@ -128,11 +128,21 @@ struct SoftminInst {
     int n_rows, n_cols;
     float lam;               // damping 1/(1+eps/rho)
     float omega;             // blend weight: out = old + omega (tilde - old)
-    // Row blocks and their column lists.  blk_row0[k]..blk_row0[k+1] are the rows
-    // of block k.  col_list == null: every block sees all columns (dense).
-    // Otherwise block k sees columns col_list[col_ptr[k] .. col_ptr[k+1]).
+    // Row blocks and their kept columns.  blk_row0[k]..blk_row0[k+1] are the rows
+    // of block k.  col_rng == null: every block sees all columns (dense).
+    // Otherwise the columns are sorted by cluster and block k sees the kept
+    // clusters as ranges of consecutive columns: entries
+    // col_rng[rng_ptr[k]] .. col_rng[rng_ptr[k+1] - 1] are (first column, its
+    // position in the block's sequence of kept columns), increasing; the last
+    // entry of a block is a sentinel (0, number of kept columns).  ColWalk
+    // below maps positions to columns.  col_list (when non-null, instead of the
+    // ranges): the same kept columns expanded one index per position, block k's
+    // at col_list[list_ptr[k] .. list_ptr[k+1]) -- cheaper to read where the
+    // clusters are small (grid cells of a few dozen points).
     const int *blk_row0;
-    const int *col_ptr;
+    const int *rng_ptr;
+    const int2 *col_rng;
+    const int *list_ptr;
     const int *col_list;
     // Cluster-tiled tensor-core form (softmin_tcc.cu, coarse-to-fine solves): the column side's points
     // centred at their cluster's centre and split into BF16 tiles of 128 columns (tcc_tiles, 32 KiB per
@@ -150,6 +160,74 @@ struct SoftminInst {
     const unsigned *tcc_bits;
     const int *tcc_blk_cl;
 };
+
+// Position -> column index over the kept ranges of one row block, for
+// positions that do not decrease from one call to the next (the walk moves
+// forward through the ranges).  start() places it at a position by binary
+// search; at(pos) requires start() <= pos < the block's number of kept
+// columns.  A step forward reads the next kRngLook entries at once
+// (independent loads, one latency for up to kRngLook ranges); the range array
+// carries kRngPad padding entries after the last block, so every entry read
+// past a block's sentinel exists.
+constexpr int kRngLook = 8, kRngPad = kRngLook + 1;
+struct ColWalk {
+    const int2 *e = nullptr;  // entry of the range holding the last position (null: dense or list)
+    const int *lst = nullptr; // the block's expanded list, when the instance has one
+    int2 cur, nxt;
+    __device__ __forceinline__ void start(const SoftminInst &I, int blk, int pos) {
+        if (I.col_list) {
+            lst = I.col_list + I.list_ptr[blk];
+            e = nullptr;
+            return;
+        }
+        if (!I.col_rng) {
+            e = nullptr;
+            return;
+        }
+        int lo = I.rng_ptr[blk], hi = I.rng_ptr[blk + 1] - 2;  // last real entry (the one before the sentinel)
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (I.col_rng[mid].y <= pos) lo = mid;
+            else hi = mid - 1;
+        }
+        e = I.col_rng + lo;
+        cur = e[0];
+        nxt = e[1];
+    }
+    __device__ __forceinline__ int at(int pos) {
+        if (lst) return lst[pos];
+        if (!e) return pos;
+        while (nxt.y <= pos) {
+            int2 w[kRngLook];  // the entries after nxt
+#pragma unroll
+            for (int q = 0; q < kRngLook; ++q) w[q] = e[2 + q];
+            // the range of pos starts at nxt or at the last w[q] (before the first that starts
+            // past pos; the block's sentinel starts past every position of the block)
+            int adv = 0;
+            bool go = true;
+#pragma unroll
+            for (int q = 0; q < kRngLook; ++q) {
+                go = go && w[q].y <= pos;
+                adv += go ? 1 : 0;
+            }
+            int2 c = nxt, n = w[0];
+#pragma unroll
+            for (int q = 0; q < kRngLook; ++q) {
+                if (adv == q + 1) c = w[q];
+                if (q + 1 < kRngLook && adv == q + 1) n = w[q + 1];
+            }
+            e += 1 + adv;
+            cur = c;
+            nxt = adv < kRngLook ? n : e[1];
+        }
+        return cur.x + (pos - cur.y);
+    }
+};
+// Number of kept columns of block blk (all columns when dense).
+__device__ __forceinline__ int kept_cols(const SoftminInst &I, int blk) {
+    if (I.col_list) return I.list_ptr[blk + 1] - I.list_ptr[blk];
+    return I.col_rng ? I.col_rng[I.rng_ptr[blk + 1] - 1].y : I.n_cols;
+}
 
 constexpr int kMaxInst = 4;
 constexpr int kTccMaxWords = 256;  // column clusters of the cluster-tiled form: at most 32 x 256

@@ -207,7 +207,9 @@ void Solver::setup_instances(const std::vector<int> &hx, const std::vector<int> 
         I.n_rows = rows[k]->n;
         I.n_cols = cols[k]->n;
         I.blk_row0 = rows_x[k] ? bx : by;
-        I.col_ptr = nullptr;
+        I.rng_ptr = nullptr;
+        I.col_rng = nullptr;
+        I.list_ptr = nullptr;
         I.col_list = nullptr;
     }
     nblk_x = (int)hx.size() - 1;
@@ -623,7 +625,11 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
             s.no_progress = 0;
             s.floor_hits = 0;
             s.delta_best = 1e300;
-            rc = s.iterate_at_blur(P, P.max_iters);
+            // at least 30 steps: the Anderson history needs a few windows to resolve the slowly
+            // contracting modes once the exponents are exact
+            otgb_params Pp = P;
+            Pp.min_iters = std::max(P.min_iters, 30);
+            rc = s.iterate_at_blur(Pp, P.max_iters);
         }
         OTGB_CUDA_TRY(cudaEventRecord(ctx_event(ctx, 4), st));
         if (rc == OTGB_OK || rc == OTGB_ENOCONV) s.S = s.divergence(s.eps_of(P.blur));

@@ -211,14 +211,13 @@ __device__ __forceinline__ void softmin3_item(const SoftminLaunch &L, int it, fl
     setup_rows3<R, TWO>(L, I, r0, r1, xr, m, c);
 
     // this item's columns: positions [cb, ce) of the block's column sequence
-    const int *list = I.col_list;
-    int c0 = 0, c1 = I.n_cols;
-    if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
+    const int nkept = kept_cols(I, blk);
     int cb = item.z, ce = item.w;
-    OTGB_DCLAMP(cb, 0, c1 - c0 + 1);
-    OTGB_DCLAMP(ce, cb, c1 - c0 + 1);
+    OTGB_DCLAMP(cb, 0, nkept + 1);
+    OTGB_DCLAMP(ce, cb, nkept + 1);
     const int ncol = ce - cb;
     const int ntiles = (ncol + kT3 - 1) / kT3;
+    ColWalk walk;
 
     // staging of one tile: lane l handles columns p0 + l + 32 u, u < kCPL.  The
     // column indices are fetched one tile ahead of the column data, so that the
@@ -230,7 +229,7 @@ __device__ __forceinline__ void softmin3_item(const SoftminLaunch &L, int it, fl
             const int p = p0 + lane + 32 * u;
             int jj = -1;
             if (p < ncol) {
-                jj = list ? list[c0 + cb + p] : cb + p;
+                jj = walk.at(cb + p);
                 OTGB_DCLAMP(jj, 0, I.n_cols);
             }
             j[u] = jj;
@@ -277,6 +276,7 @@ __device__ __forceinline__ void softmin3_item(const SoftminLaunch &L, int it, fl
 #pragma unroll
         for (int k = 0; k < R; ++k) mx[k] = -INFINITY;
         int jn[kCPL];
+        walk.start(I, blk, cb);
         if (ntiles > 0) { load_idx(0, jn); load_col(jn, q, pot); store_col(0, q, pot); }
         if (ntiles > 1) load_idx(kT3, jn);
         __syncwarp();
@@ -313,6 +313,7 @@ __device__ __forceinline__ void softmin3_item(const SoftminLaunch &L, int it, fl
     for (int p = 0; p < P; ++p) Mn[p] = pack2(-m[2 * p], -m[2 * p + 1]);
 
     int jn[kCPL];
+    walk.start(I, blk, cb);
     if (ntiles > 0) { load_idx(0, jn); load_col(jn, q, pot); store_col(0, q, pot); }
     if (ntiles > 1) load_idx(kT3, jn);
     __syncwarp();
@@ -614,16 +615,14 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
         S.xs[KPD][t] = make_float2(1.f, -m);
     }
 
-    // ---- columns of this item
-    const int *list = I.col_list;
-    int c0 = 0, c1 = I.n_cols;
-    if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
+    // ---- columns of this item: positions [cb, ce) of the block's columns (never split for D > 3)
+    const int nkept = kept_cols(I, blk);
     int cb = item.z, ce = item.w;
-    OTGB_DCLAMP(cb, 0, c1 - c0 + 1);
-    OTGB_DCLAMP(ce, cb, c1 - c0 + 1);
-    c0 += cb;  // this item sees positions [cb, ce) of the block's columns (never split for D > 3)
+    OTGB_DCLAMP(cb, 0, nkept + 1);
+    OTGB_DCLAMP(ce, cb, nkept + 1);
     const int ncol = ce - cb;
     const int ntiles = (ncol + kBN - 1) / kBN;
+    ColWalk walk;
 
     // copy/repack roles: chunk ch (coordinates 8 ch .. 8 ch + 7) of columns colb and colb + 32
     const int ch = t & 7, colb = t >> 3;
@@ -636,7 +635,7 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
             const int p = tile * kBN + colb + 32 * q;
             int jj = -1;
             if (tile < ntiles && p < ncol) {
-                jj = list ? list[c0 + p] : p;
+                jj = walk.at(cb + p);
                 OTGB_DCLAMP(jj, 0, I.n_cols);
             }
             j[q] = jj;
@@ -731,6 +730,7 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
         for (int i = 0; i < 8; ++i) res[i] = MAXP ? -INFINITY : 0.f;
         if (ntiles == 0) return;
         int jn[2];
+        walk.start(I, blk, cb);
         load_idx(0, jn);
         issue(jn);
         cp_async_commit();
@@ -831,16 +831,15 @@ __global__ void __launch_bounds__(kFbThreads) softmin_fallback_kernel(const __gr
         const SoftminInst &I = L.inst[fb.x];
         OTGB_DCLAMP(fb.y, 0, I.n_rows);
         const int r = fb.y, blk = fb.z;
-        const int *list = I.col_list;
-        int c0 = 0, c1 = I.n_cols;
-        if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
+        const int n = kept_cols(I, blk);
+        ColWalk walk;
         __syncthreads();  // the previous row is done with xs and the reductions
         if (t < stride) xs[t] = I.rows[(size_t)r * stride + t];
         __syncthreads();
         const float eps = L.eps, s = L.s;
         const int n4 = stride >> 2;
         auto term = [&](int p) -> float {
-            int j = list ? list[c0 + p] : p;
+            int j = walk.at(p);
             OTGB_DCLAMP(j, 0, I.n_cols);
             const float4 *yj = reinterpret_cast<const float4 *>(I.cols + (size_t)j * stride);
             float d2 = 0.f, lw;
@@ -861,8 +860,8 @@ __global__ void __launch_bounds__(kFbThreads) softmin_fallback_kernel(const __gr
             }
             return s * (fmaf(eps, lw, I.col_pot[j]) - 0.5f * d2);
         };
-        const int n = c1 - c0;
         float m = -INFINITY;
+        walk.start(I, blk, t);
         for (int p = t; p < n; p += kFbThreads) m = fmaxf(m, term(p));
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) redf[wid] = m;
@@ -871,6 +870,7 @@ __global__ void __launch_bounds__(kFbThreads) softmin_fallback_kernel(const __gr
 #pragma unroll
         for (int k = 1; k < kFbThreads / 32; ++k) m = fmaxf(m, redf[k]);
         double acc = 0.0;
+        walk.start(I, blk, t);
         if (m > -INFINITY)
             for (int p = t; p < n; p += kFbThreads) acc += (double)exp2f(term(p) - m);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

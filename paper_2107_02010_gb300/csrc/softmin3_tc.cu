@@ -192,15 +192,14 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
     }
 
     // ---- columns of this item
-    const int *list = I.col_list;
-    int c0 = 0, c1 = I.n_cols;
-    if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
+    const int nkept = kept_cols(I, blk);
     int cb = item.z, ce = item.w;
-    OTGB_DCLAMP(cb, 0, c1 - c0 + 1);
-    OTGB_DCLAMP(ce, cb, c1 - c0 + 1);
+    OTGB_DCLAMP(cb, 0, nkept + 1);
+    OTGB_DCLAMP(ce, cb, nkept + 1);
     const int ncol = ce - cb;
     const int ntiles = (ncol + kN - 1) / kN;
-    (void)c1;
+    ColWalk walk;
+    walk.start(I, blk, cb);
 
     // thread tid < kN stages column tid of each tile
     const bool stager = tid < kN;
@@ -208,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
         const int pp = tile * kN + tid;
         int jj = -1;
         if (stager && tile < ntiles && pp < ncol) {
-            jj = list ? list[c0 + cb + pp] : cb + pp;
+            jj = walk.at(cb + pp);
             OTGB_DCLAMP(jj, 0, I.n_cols);
         }
         return jj;

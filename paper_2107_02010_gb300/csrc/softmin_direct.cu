@@ -37,6 +37,7 @@ template <int D4, bool P1>
 __global__ void __launch_bounds__(kP1R) softmin_direct_kernel(const __grid_constant__ SoftminLaunch L, int D) {
     __shared__ float ys[kP1C][D4];
     __shared__ float yh[kP1C];  // log2 w_j + s pot_j (-inf: no column)
+    __shared__ int yj[kP1C];    // column index of each tile column
     __shared__ float red[kP1R / 32];
     int4 item = L.items[blockIdx.x];
     OTGB_DCLAMP(item.x, 0, L.n_inst);
@@ -54,37 +55,41 @@ __global__ void __launch_bounds__(kP1R) softmin_direct_kernel(const __grid_const
 #pragma unroll
     for (int d = 0; d < D4; ++d) x[d] = (valid && d < ncoord) ? I.rows[(size_t)r * D4 + d] : 0.f;
 
-    const int *list = I.col_list;
-    int c0 = 0, c1 = I.n_cols;
-    if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
+    const int nkept = kept_cols(I, blk);
     int cb = item.z, ce = item.w;
-    OTGB_DCLAMP(cb, 0, c1 - c0 + 1);
-    OTGB_DCLAMP(ce, cb, c1 - c0 + 1);
+    OTGB_DCLAMP(cb, 0, nkept + 1);
+    OTGB_DCLAMP(ce, cb, nkept + 1);
     const int ncol = ce - cb;
     const float s = L.s;
     float m = -INFINITY, acc = 0.f;
+    // thread t < kP1C finds column p0 + t of each tile
+    ColWalk walk;
+    walk.start(I, blk, cb);
     for (int p0 = 0; p0 < ncol; p0 += kP1C) {
         const int nc = min(kP1C, ncol - p0);
+        __syncthreads();
+        if (t < kP1C) {
+            float h = -INFINITY;
+            int j = -1;
+            if (t < nc) {
+                j = walk.at(cb + p0 + t);
+                OTGB_DCLAMP(j, 0, I.n_cols);
+                const float lw = D <= 3 ? I.cols[(size_t)j * 4 + 3] : I.col_logw[j];
+                h = lw == -INFINITY ? -INFINITY : fmaf(kLog2e, lw, s * I.col_pot[j]);
+            }
+            yj[t] = j;
+            yh[t] = h;
+        }
         __syncthreads();
         for (int e = t; e < kP1C * D4; e += kP1R) {
             const int c = e / D4, d = e - c * D4;
             float v = 0.f;
             if (c < nc && d < ncoord) {
-                int j = list ? list[c0 + cb + p0 + c] : cb + p0 + c;
+                int j = yj[c];
                 OTGB_DCLAMP(j, 0, I.n_cols);
                 v = I.cols[(size_t)j * D4 + d];
             }
             ys[c][d] = v;
-        }
-        if (t < kP1C) {
-            float h = -INFINITY;
-            if (t < nc) {
-                int j = list ? list[c0 + cb + p0 + t] : cb + p0 + t;
-                OTGB_DCLAMP(j, 0, I.n_cols);
-                const float lw = D <= 3 ? I.cols[(size_t)j * 4 + 3] : I.col_logw[j];
-                h = lw == -INFINITY ? -INFINITY : fmaf(kLog2e, lw, s * I.col_pot[j]);
-            }
-            yh[t] = h;
         }
         __syncthreads();
         for (int c = 0; c < nc; ++c) {

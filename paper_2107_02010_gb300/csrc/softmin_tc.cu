@@ -186,13 +186,13 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
     __syncthreads();  // S.h[0] is reused for the columns
 
     // ---- columns of this item
-    const int *list = I.col_list;
-    int c0 = 0, c1 = I.n_cols;
-    if (list) { c0 = I.col_ptr[blk]; c1 = I.col_ptr[blk + 1]; }
+    const int nkept = kept_cols(I, blk);
     int cb = item.z, ce = item.w;
-    OTGB_DCLAMP(cb, 0, c1 - c0 + 1);
-    OTGB_DCLAMP(ce, cb, c1 - c0 + 1);
+    OTGB_DCLAMP(cb, 0, nkept + 1);
+    OTGB_DCLAMP(ce, cb, nkept + 1);
     const int ncol = ce - cb;
+    ColWalk walk;
+    walk.start(I, blk, cb);
     const int ntiles = (ncol + kTcN - 1) / kTcN;
 
     // Staging of a column tile, software-pipelined over three tiles: the
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(128, 2) softmin_tc_kernel(const __grid_constan
             const int p = p0 + colb + 16 * k;
             int jj = -1;
             if (tile < ntiles && p < ncol) {
-                jj = list ? list[c0 + cb + p] : cb + p;
+                jj = walk.at(cb + p);
                 OTGB_DCLAMP(jj, 0, I.n_cols);
             }
             j[k] = jj;
