@@ -514,7 +514,7 @@ constexpr int kXS = kBM + 2;  // float2 stride of a k-pair of X (spreads the sta
 
 struct GenSmem {
     float2 xs[kKP][kXS];     // X pairs; pair KPD = (1, -m_i)
-    float2 ys[2][kKP][kBN];  // yt pairs, chunk-swizzled; pair KPD = (H_j, 1)
+    float2 ys[3][kKP][kBN];  // yt pairs, chunk-swizzled; pair KPD = (H_j, 1); three tiles in flight
     float raw[kBN][64];      // raw column coordinates of the next tile, as copied
     float rlw[kBN];
     float rpot[kBN];
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
     if (t == 0)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(&S.tbar)),
                      "r"(kNTg));
-    uint32_t tphase = 0u;
+    int nphase = 0;  // tile-barrier phases this thread has arrived at so far (all sweeps)
     bool timed_out = false;
 
     // ---- rows: raw pairs, centre (mean), X = s (x - c), |xt|^2 / 2, fold pair
@@ -729,6 +729,13 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
 #pragma unroll
         for (int i = 0; i < 8; ++i) res[i] = MAXP ? -INFINITY : 0.f;
         if (ntiles == 0) return;
+        // Three column tiles in flight: tiles t and t+1 are repacked while the CTA multiplies
+        // tile t, and the repack of tile t+2 (into the buffer of tile t-1) needs only that every
+        // thread has finished iteration t-1 -- one tile of slack, so a warp that is ahead does not
+        // wait for the slowest warp's products of the same tile.  Iteration t: products(t); wait
+        // for phase t-1 (all threads past repack(t+1), hence past products(t-1)); repack(t+2);
+        // arrive at phase t; fold tile t into the row sums.  (Checked on a CPU model of the
+        // mbarrier over random interleavings before it ran on a GPU.)
         int jn[2];
         walk.start(I, blk, cb);
         load_idx(0, jn);
@@ -740,21 +747,29 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
         issue(jn);  // tile 1 (nothing past the end)
         cp_async_commit();
         load_idx(2, jn);
+        cp_async_wait0();
+        repack(1, 1);
+        issue(jn);  // tile 2
+        cp_async_commit();
+        load_idx(3, jn);
         __syncthreads();
+        const int ph0 = nphase;
         for (int tt = 0; tt < ntiles; ++tt) {
-            const int buf = tt & 1;
+            const int buf = tt % 3;
             u64 acc[8][4];
             products(buf, acc);
-            if (tt + 1 < ntiles) {
-                cp_async_wait0();  // this thread's copies of tile tt+1
-                repack(buf ^ 1, tt + 1);
-                if (tt + 2 < ntiles) issue(jn);  // into the raw slots just consumed
-                cp_async_commit();
-                load_idx(tt + 3, jn);
+            if (tt >= 1 && tt + 1 < ntiles) {  // phase tt - 1 was arrived at (tt + 1 < ntiles)
+                if (!mbar_wait_parity(&S.tbar, (uint32_t)((ph0 + tt - 1) & 1))) timed_out = true;
             }
-            // tile barrier split in two: arrive once ys[buf] is read and ys[buf ^ 1]
-            // written, fold the accumulators into the row sums, then wait
-            mbar_arrive(&S.tbar);
+            if (tt + 2 < ntiles) {
+                cp_async_wait0();  // this thread's copies of tile tt+2
+                repack((tt + 2) % 3, tt + 2);
+                if (tt + 3 < ntiles) issue(jn);  // into the raw slots just consumed
+                cp_async_commit();
+                load_idx(tt + 4, jn);
+                mbar_arrive(&S.tbar);  // phase ph0 + tt
+                ++nphase;
+            }
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 float e[4];
@@ -767,8 +782,6 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
                 if (MAXP) res[i] = fmaxf(res[i], fmaxf(fmaxf(e[0], e[1]), fmaxf(e[2], e[3])));
                 else res[i] += (ex2(e[0]) + ex2(e[1])) + (ex2(e[2]) + ex2(e[3]));
             }
-            if (!mbar_wait_parity(&S.tbar, tphase)) timed_out = true;
-            tphase ^= 1u;
         }
         cp_async_wait0();
     };
