@@ -47,7 +47,10 @@ def _net(ctx, D, H, theta, norm):
     return net
 
 
-@pytest.mark.parametrize("D,H,n", [(60, 256, 1000), (60, 256, 128), (7, 128, 333), (3, 256, 2049)])
+# inference runs the fused kernel (all layers per 128-row tile on chip); the sizes cover one tile, a ragged
+# tail, inputs whose rows are not 16-byte aligned (D = 7, 3), H = 128, and many tiles per persistent CTA
+@pytest.mark.parametrize("D,H,n", [(60, 256, 1000), (60, 256, 128), (7, 128, 333), (3, 256, 2049),
+                                   (60, 256, 200_001)])
 def test_forward_matches_oracle(ctx, D, H, n):
     theta, x, _, norm = _setup(D, H, n, seed=n + D)
     net = _net(ctx, D, H, theta, norm)
