@@ -548,6 +548,102 @@ def run_barycenter(args):
     return 0
 
 
+# -------------------------------------------------------------------- warm --
+def run_warm(args):
+    """Learned warm start against a fixed atlas, time-to-solve: a 300k-fiber
+    atlas; `--warm-train` training subjects and `--warm-test` test subjects of
+    uneven sizes (uniform in [100k, 400k] fibers, each subject's bundles
+    displaced by its own perturbation); the network (60 -> 256 -> 256 -> 256 ->
+    1) trained on the f potentials of plain solves of the training subjects.
+    One step = every test subject solved by the plain multiscale FP32 form and
+    by the warm-started form, both with the stopping rule tol = 1e-4 (the S they
+    return is checked against a tight reference solve, tol 1e-9, at 1e-5
+    relative).  Times are device times of the solves (the warm one including
+    the network's inference)."""
+    import torch
+    from paper_2107_02010_gb300 import otgb, synth
+
+    BLUR, REACH = 2.0, 20.0
+
+    def P(n, **kw):
+        base = dict(blur=BLUR, reach=REACH, scaling=0.5, multiscale=1, cluster=1, k_clusters=1000,
+                    kmeans_iters=10, tol=1e-4, max_iters=3000)
+        base.update(kw)
+        return otgb.default_params(**base)
+
+    t_start = time.time()
+    ctx = otgb.Context()
+    ctrl = synth.bundle_centrelines()
+    y, b, _ = synth.fiber_bundles(300000, seed=10, ctrl=ctrl)
+    yt, bt = torch.from_numpy(y).cuda(), torch.from_numpy(b).cuda()
+    rng = np.random.default_rng(0)
+    X, F = [], []
+    b_atlas = None
+    for s in range(args.warm_train):
+        n = int(rng.integers(100000, 400001))
+        x, a, _ = synth.fiber_bundles(n, seed=100 + s, ctrl=ctrl, perturb=3.0)
+        xt, at = torch.from_numpy(x).cuda(), torch.from_numpy(a).cuda()
+        r = otgb.sinkhorn_divergence(ctx, xt, at, yt, bt, P(n, tol=1e-8), want_self=True)
+        X.append(xt)
+        F.append(r["f"])
+        if b_atlas is None:
+            b_atlas = r["b_self"].clone()
+    Xc, Fc = torch.cat(X), torch.cat(F)
+    t_targets = time.time() - t_start
+    net = otgb.Mlp(ctx, 60, 256, seed=7)
+    net.fit_normalization(Xc, Fc)
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for e in range(args.warm_epochs):
+        lr = 1e-5 + 0.5 * (1e-3 - 1e-5) * (1 + np.cos(np.pi * e / args.warm_epochs))
+        losses.append(net.train_epoch(Xc, Fc, 16384, lr, seed=e))
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    tests = []
+    f0_err = []
+    for s in range(args.warm_test):
+        n = int(rng.integers(100000, 400001))
+        x, a, _ = synth.fiber_bundles(n, seed=300 + s, ctrl=ctrl, perturb=3.0)
+        xt, at = torch.from_numpy(x).cuda(), torch.from_numpy(a).cuda()
+        ref = otgb.sinkhorn_divergence(ctx, xt, at, yt, bt, P(n, tol=1e-9, max_iters=6000))
+        f0_err.append(float((net.infer(xt) - ref["f"]).abs().median()) / (BLUR ** 2))
+        tests.append((n, xt, at, ref))
+    l0 = otgb.kernel_launches()
+    acc = {"plain": [0, 0.0, 0.0], "warm": [0, 0.0, 0.0]}
+    fell_back = 0
+    for k in range(args.warmup + args.steps):
+        for n, xt, at, ref in tests:
+            rp = otgb.sinkhorn_divergence(ctx, xt, at, yt, bt, P(n))
+            rw = otgb.sinkhorn_divergence_warm(ctx, net, xt, at, yt, bt, P(n), b_atlas=b_atlas)
+            if k < args.warmup:
+                continue
+            fell_back += int(rw["stats"]["warm_start"] == 2)
+            for key, r, ms in (("plain", rp, rp["stats"]["total_ms"]), ("warm", rw, rw["stats"]["warm_ms"])):
+                acc[key][0] += r["stats"]["iters_total"]
+                acc[key][1] += ms
+                acc[key][2] = max(acc[key][2], abs(r["S"] - ref["S"]) / abs(ref["S"]))
+    ns = args.steps * len(tests)
+    warm_s = acc["warm"][1] / ns / 1e3
+    plain_s = acc["plain"][1] / ns / 1e3
+    line = {"metric": "time-to-solve, learned warm start", "workload": "warm", "value": warm_s, "unit": "s",
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "learned warm start against a fixed 300k-fiber atlas (60-D fibers, blur 2, reach 20, "
+                                   "k-means 1000 clusters); %d training and %d test subjects of 100k-400k fibers; "
+                                   "network 60-256-256-256-1 trained %d epochs" % (
+                                       args.warm_train, args.warm_test, args.warm_epochs)},
+            "per_subject": {"plain_s": plain_s, "warm_s": warm_s, "plain_steps": acc["plain"][0] / ns,
+                            "warm_steps": acc["warm"][0] / ns, "plain_max_rel_S_err": acc["plain"][2],
+                            "warm_max_rel_S_err": acc["warm"][2], "warm_fell_back": fell_back},
+            "plain_over_warm": plain_s / warm_s,
+            "f0_median_abs_err_in_eps": f0_err, "train_loss_first_last": [losses[0], losses[-1]],
+            "targets_s": t_targets, "training_s": t_train,
+            "gpu_launches": int(otgb.kernel_launches() - l0)}
+    print(json.dumps(line))
+    return 0
+
+
 # --------------------------------------------------------------------- mlp --
 def run_mlp(args):
     """Warm-start network throughput: inference over n rows and one training
@@ -640,7 +736,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fibers", choices=["fibers", "density", "mlp", "barycenter", "rates"])
+    ap.add_argument("--workload", default="fibers",
+                    choices=["fibers", "density", "mlp", "barycenter", "rates", "warm"])
+    ap.add_argument("--warm-train", type=int, default=8)
+    ap.add_argument("--warm-test", type=int, default=3)
+    ap.add_argument("--warm-epochs", type=int, default=30)
     ap.add_argument("--iters", type=int, default=5, help="barycenter: gradient steps")
     ap.add_argument("--n", type=int, default=0, help="fibers: points per side (1,000,000); mlp: rows (1,048,576)")
     ap.add_argument("--grid", type=int, default=64)
@@ -668,6 +768,8 @@ def main():
         return run_barycenter(args)
     if args.workload == "rates":
         return run_rates(args)
+    if args.workload == "warm":
+        return run_warm(args)
     return run_fibers(args)
 
 
