@@ -556,9 +556,9 @@ def run_warm(args):
     displaced by its own perturbation); the network (60 -> 256 -> 256 -> 256 ->
     1) trained on the f potentials of plain solves of the training subjects.
     One step = every test subject solved by the plain multiscale FP32 form and
-    by the warm-started form, both with the stopping rule tol = 1e-4 (the S they
-    return is checked against a tight reference solve, tol 1e-9, at 1e-5
-    relative).  Times are device times of the solves (the warm one including
+    by the warm-started form, both with the stopping rule tol = 1e-4 checked
+    every 3 steps (the S they return is checked against a tight reference
+    solve, tol 1e-9, at 1e-5 relative).  Times are device times of the solves (the warm one including
     the network's inference)."""
     import torch
     from paper_2107_02010_gb300 import otgb, synth
@@ -567,7 +567,7 @@ def run_warm(args):
 
     def P(n, **kw):
         base = dict(blur=BLUR, reach=REACH, scaling=0.5, multiscale=1, cluster=1, k_clusters=1000,
-                    kmeans_iters=10, tol=1e-4, max_iters=3000)
+                    kmeans_iters=10, tol=1e-4, max_iters=3000, check_every=3)
         base.update(kw)
         return otgb.default_params(**base)
 
