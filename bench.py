@@ -647,8 +647,9 @@ def run_warm(args):
 # --------------------------------------------------------------------- mlp --
 def run_mlp(args):
     """Warm-start network throughput: inference over n rows and one training
-    epoch over n rows (batches of 16384), FLOPs counted as 2 per multiply-add of
-    the four layers (input padded to 64); training = 3 x forward."""
+    epoch over n rows (batches of `--train-batch`, default 16384), FLOPs
+    counted as 2 per multiply-add of the four layers (input padded to 64);
+    training = 3 x forward."""
     import torch
     from paper_2107_02010_gb300 import otgb
 
@@ -660,9 +661,10 @@ def run_mlp(args):
     x = torch.from_numpy(r.normal(0, 1, (n, D)).astype(np.float32)).cuda()
     f = torch.from_numpy(r.normal(0, 1, n).astype(np.float32)).cuda()
     fwd = 2.0 * n * (64 * H + 2 * H * H + H)
+    tb = args.train_batch
     for _ in range(args.warmup):
         net.infer(x)
-        net.train_epoch(x, f, 16384, 1e-4, seed=0)
+        net.train_epoch(x, f, tb, 1e-4, seed=0)
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     l0 = otgb.kernel_launches()
@@ -673,7 +675,7 @@ def run_mlp(args):
     ev[1].record(st)
     ev[2].record(st)
     for k in range(args.steps):
-        net.train_epoch(x, f, 16384, 1e-4, seed=k + 1)
+        net.train_epoch(x, f, tb, 1e-4, seed=k + 1)
     ev[3].record(st)
     torch.cuda.synchronize()
     inf_ms = ev[0].elapsed_time(ev[1]) / args.steps
@@ -682,7 +684,7 @@ def run_mlp(args):
     line = {"metric": "warm-start network TFLOP/s", "workload": "mlp", "unit": "TFLOP/s",
             "value": fwd / inf_ms / 1e9, "steps": args.steps, "warmup": args.warmup, "dtype": "bf16",
             "data": "synthetic", "higher_is_better": True,
-            "config": {"workload": "MLP %d->%d->%d->%d->1 SiLU, %d rows" % (D, H, H, H, n)},
+            "config": {"workload": "MLP %d->%d->%d->%d->1 SiLU, %d rows" % (D, H, H, H, n), "train_batch": tb},
             "inference_ms": inf_ms, "inference_tflops": fwd / inf_ms / 1e9,
             "train_epoch_ms": tr_ms, "train_tflops": 3 * fwd / tr_ms / 1e9,
             "roofline": {"bound": "tensor", "peak": peak, "unit": "TFLOP/s",
@@ -741,6 +743,7 @@ def main():
     ap.add_argument("--warm-train", type=int, default=8)
     ap.add_argument("--warm-test", type=int, default=3)
     ap.add_argument("--warm-epochs", type=int, default=30)
+    ap.add_argument("--train-batch", type=int, default=16384)
     ap.add_argument("--iters", type=int, default=5, help="barycenter: gradient steps")
     ap.add_argument("--n", type=int, default=0, help="fibers: points per side (1,000,000); mlp: rows (1,048,576)")
     ap.add_argument("--grid", type=int, default=64)
