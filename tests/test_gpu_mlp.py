@@ -47,10 +47,11 @@ def _net(ctx, D, H, theta, norm):
     return net
 
 
-# inference runs the fused kernel (all layers per 128-row tile on chip); the sizes cover one tile, a ragged
-# tail, inputs whose rows are not 16-byte aligned (D = 7, 3), H = 128, and many tiles per persistent CTA
-@pytest.mark.parametrize("D,H,n", [(60, 256, 1000), (60, 256, 128), (7, 128, 333), (3, 256, 2049),
-                                   (60, 256, 200_001)])
+# inference runs the fused kernel (all layers per 128-row tile on chip); the sizes cover a single row, one
+# tile, ragged tails of one row, inputs whose rows are not 16-byte aligned (D = 7, 3), H = 128, and many tiles
+# per persistent CTA
+@pytest.mark.parametrize("D,H,n", [(60, 256, 1000), (60, 256, 128), (60, 256, 1), (60, 128, 129), (7, 128, 333),
+                                   (3, 256, 2049), (60, 256, 200_001)])
 def test_forward_matches_oracle(ctx, D, H, n):
     theta, x, _, norm = _setup(D, H, n, seed=n + D)
     net = _net(ctx, D, H, theta, norm)
@@ -61,6 +62,23 @@ def test_forward_matches_oracle(ctx, D, H, n):
     scale = np.sqrt(np.mean(o ** 2)) + 1.0
     assert np.max(err) <= 3e-2 * scale, (np.max(err), scale)
     assert np.mean(err) <= 1e-2 * scale, (np.mean(err), scale)
+
+
+def test_forward_unaligned_input_is_identical(ctx):
+    # D % 4 == 0 but the rows start 4 bytes past a 16-byte boundary: the fused kernel reads the input directly
+    # instead of with one bulk copy per tile; the normalisation is the same float arithmetic, so the outputs
+    # are bit-identical
+    D, H, n = 60, 256, 300
+    theta, x, _, norm = _setup(D, H, n, seed=11)
+    net = _net(ctx, D, H, theta, norm)
+    xa = torch.from_numpy(x).cuda()
+    buf = torch.empty(n * D + 1, dtype=torch.float32, device="cuda")
+    xu = buf[1:].view(n, D)
+    xu.copy_(xa)
+    assert xu.data_ptr() % 16 != 0
+    pa = net.infer(xa)
+    pu = net.infer(xu)
+    assert torch.equal(pa, pu)
 
 
 @pytest.mark.parametrize("D,H,n", [(60, 256, 777), (60, 256, 4096), (5, 128, 300)])
