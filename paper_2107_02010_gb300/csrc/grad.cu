@@ -12,6 +12,9 @@
 //
 // Each CTA owns 128 rows (one per thread, the row's point and its gradient in
 // registers); column tiles are staged in shared memory and read as broadcasts.
+// Two forms: every pair (sinkhorn_grad_x, from the caller's points and duals),
+// and the kept cluster pairs of a solve's last truncation (the barycenter's
+// steps, from inside the solve).
 // Per pair: the direct difference form of the cost (no cancellation), one
 // ex2, and the weighted difference accumulated with an online maximum (a term
 // larger than every earlier one rescales the running sums), so no shift has
@@ -20,6 +23,7 @@
 #include <cstring>
 #include <vector>
 
+#include "multiscale.cuh"
 #include "solver.cuh"
 
 namespace otgb {
@@ -165,6 +169,155 @@ GradArgs grad_args(const float *x, const float *alpha, int N, const float *y, co
     return A;
 }
 
+// ---- the same gradient over the kept cluster pairs of a solve (internal order)
+// One CTA per row block of the first measure (the solve's own blocks, at most
+// 128 rows, one per thread); part 0 walks the block's kept columns of the
+// second measure (instance 3: rows x against (y, beta, g)), part 1 those of the
+// first (instance 0: rows x against (x, alpha, a)).  The terms left out are
+// those the truncation dropped, each below e^-tau of its row's total.
+struct SpGradArgs {
+    SoftminInst inst[2];
+    const float *rpot[2];  // f, a (internal order)
+    const float *cpot[2];  // g, a
+    float sign[2];
+    const float *row_w;    // alpha (internal order)
+    const int *perm;       // internal position -> caller index (null: identity)
+    int n, D, stride, small, p1;
+    float s;               // log2(e) / eps
+    float scale;
+    int accumulate;
+    float *grad;           // caller's order, n x D
+};
+
+template <int D4>
+__global__ void __launch_bounds__(kGR) grad_sparse_kernel(const __grid_constant__ SpGradArgs A) {
+    __shared__ float ys[kGC][D4];
+    __shared__ float yt[kGC];
+    __shared__ int jidx[kGC];
+    const int t = threadIdx.x, blk = blockIdx.x;
+    const int D = A.D;
+    int r0 = A.inst[0].blk_row0[blk], r1 = A.inst[0].blk_row0[blk + 1];
+    OTGB_DCLAMP(r0, 0, A.n + 1);
+    OTGB_DCLAMP(r1, r0, min(A.n, r0 + kGR) + 1);
+    const int i = r0 + t;
+    const bool valid = i < r1;
+    const int rs = A.small ? 4 : A.stride;  // floats per point
+    float x[D4], out[D4];
+#pragma unroll
+    for (int d = 0; d < D4; ++d) {
+        x[d] = (valid && d < D) ? A.inst[0].rows[(size_t)i * rs + d] : 0.f;
+        out[d] = 0.f;
+    }
+    for (int q = 0; q < 2; ++q) {
+        const SoftminInst &I = A.inst[q];
+        const int nk = kept_cols(I, blk);
+        ColWalk walk;
+        if (t < kGC) walk.start(I, blk, t);
+        const float rt = valid ? A.s * A.rpot[q][i] : 0.f;
+        float m = -INFINITY;
+        float v[D4];
+#pragma unroll
+        for (int d = 0; d < D4; ++d) v[d] = 0.f;
+        for (int p0 = 0; p0 < nk; p0 += kGC) {
+            const int nc = min(kGC, nk - p0);
+            __syncthreads();  // the previous tile is consumed
+            if (t < kGC) {
+                int j = -1;
+                float ct = -INFINITY;
+                if (t < nc) {
+                    j = walk.at(p0 + t);
+                    OTGB_DCLAMP(j, 0, I.n_cols);
+                    const float lw = A.small ? I.cols[(size_t)j * 4 + 3] : I.col_logw[j];
+                    if (lw > -INFINITY) ct = lw * 1.4426950408889634f + A.s * A.cpot[q][j];
+                }
+                jidx[t] = j;
+                yt[t] = ct;
+            }
+            __syncthreads();
+            for (int e = t; e < kGC * D4; e += kGR) {
+                const int c = e / D4, d = e - c * D4;
+                const int j = jidx[c];
+                ys[c][d] = (j >= 0 && d < D) ? I.cols[(size_t)j * rs + d] : 0.f;
+            }
+            __syncthreads();
+            for (int c = 0; c < nc; ++c) {
+                const float ct = yt[c];
+                if (ct == -INFINITY) continue;  // the same column for every thread
+                float sq = 0.f;
+#pragma unroll
+                for (int d = 0; d < D4; ++d) {
+                    const float df = x[d] - ys[c][d];
+                    sq = fmaf(df, df, sq);
+                }
+                const float dist = A.p1 ? sqrtf(sq) : 0.f;
+                const float e = A.p1 ? fmaf(-A.s, dist, rt + ct) : fmaf(-0.5f * A.s, sq, rt + ct);
+                if (e > m) {
+                    const float sc = ex2g(m - e);
+#pragma unroll
+                    for (int d = 0; d < D4; ++d) v[d] *= sc;
+                    m = e;
+                }
+                float w = ex2g(e - m);
+                if (A.p1) w = dist > 0.f ? w / dist : 0.f;
+#pragma unroll
+                for (int d = 0; d < D4; ++d) v[d] = fmaf(w, x[d] - ys[c][d], v[d]);
+            }
+        }
+        if (m > -INFINITY) {
+            const float em = A.sign[q] * exp2f(m);
+#pragma unroll
+            for (int d = 0; d < D4; ++d) out[d] = fmaf(em, v[d], out[d]);
+        }
+    }
+    if (!valid) return;
+    int gi = A.perm ? A.perm[i] : i;
+    OTGB_DCLAMP(gi, 0, A.n);
+    const float aw = A.row_w[i] * A.scale;
+    for (int d = 0; d < D; ++d) {
+        float r = aw * out[d];
+        if (A.accumulate) r += A.grad[(size_t)gi * D + d];
+        A.grad[(size_t)gi * D + d] = r;
+    }
+}
+
+void grad_sparse_run(const Solver &s, double eps, const GradRequest &gr, cudaStream_t st) {
+    SpGradArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.inst[0] = s.launch.inst[3];  // rows x against (y, beta, g)
+    A.inst[1] = s.launch.inst[0];  // rows x against (x, alpha, a)
+    A.rpot[0] = s.pf[s.cur];
+    A.cpot[0] = s.pg[s.cur];
+    A.rpot[1] = s.pa[s.cur];
+    A.cpot[1] = s.pa[s.cur];
+    A.sign[0] = 1.f;
+    A.sign[1] = -1.f;
+    A.row_w = s.X.w;
+    A.perm = s.X.perm;
+    A.n = s.X.n;
+    A.D = s.D;
+    A.stride = s.X.stride;
+    A.small = s.D <= 3 ? 1 : 0;
+    A.p1 = s.p == 1 ? 1 : 0;
+    A.s = (float)(1.4426950408889634 / eps);
+    A.scale = gr.scale;
+    A.accumulate = gr.accumulate;
+    A.grad = gr.grad;
+    require(s.nblk_x >= 1 && A.inst[0].blk_row0 && A.inst[1].blk_row0, "gradient: the solve has no row blocks",
+            OTGB_EINTERNAL);
+    const int D4 = (s.D + 3) & ~3;
+    switch (D4) {
+#define OTGB_SGRAD_CASE(K) \
+    case K: grad_sparse_kernel<K><<<s.nblk_x, kGR, 0, st>>>(A); break;
+        OTGB_SGRAD_CASE(4) OTGB_SGRAD_CASE(8) OTGB_SGRAD_CASE(12) OTGB_SGRAD_CASE(16)
+        OTGB_SGRAD_CASE(20) OTGB_SGRAD_CASE(24) OTGB_SGRAD_CASE(28) OTGB_SGRAD_CASE(32)
+        OTGB_SGRAD_CASE(36) OTGB_SGRAD_CASE(40) OTGB_SGRAD_CASE(44) OTGB_SGRAD_CASE(48)
+        OTGB_SGRAD_CASE(52) OTGB_SGRAD_CASE(56) OTGB_SGRAD_CASE(60) OTGB_SGRAD_CASE(64)
+#undef OTGB_SGRAD_CASE
+        default: throw Error{OTGB_EINVAL, "gradient: D must be in [1, 64]"};
+    }
+    OTGB_CHECK_LAUNCH();
+}
+
 // x_i <- x_i - lr G_i / alpha_i (rows with alpha_i = 0 stay)
 __global__ void descent_kernel(float *x, const float *alpha, const float *G, int n, int D, float lr) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -174,6 +327,11 @@ __global__ void descent_kernel(float *x, const float *alpha, const float *G, int
 }
 
 }  // namespace
+
+void grad_sparse_launch(const Solver &s, double eps, const GradRequest &gr, cudaStream_t st) {
+    grad_sparse_run(s, eps, gr, st);
+}
+
 }  // namespace otgb
 
 using namespace otgb;
@@ -230,7 +388,6 @@ extern "C" int sinkhorn_barycenter(otgb_ctx *ctx, float *x, const float *alpha, 
             gk[k] = ws.get<float>("bary:g" + s, Ms[k]);
             bk[k] = ws.get<float>("bary:b" + s, Ms[k]);
         }
-        const double eps = P.p == 1 ? P.blur : P.blur * P.blur;
         for (int it = 0; it <= iters; ++it) {
             double Ssum = 0.0;
             const bool last = it == iters;
@@ -246,14 +403,13 @@ extern "C" int sinkhorn_barycenter(otgb_ctx *ctx, float *x, const float *alpha, 
                     Pk.sigma_start = P.blur;
                 }
                 float *f = fk[k], *g = gk[k], *a = ak[k];
-                const int rc = sinkhorn_divergence(ctx, x, alpha, N, ys[k], betas[k], Ms[k], D, &Pk, &S, f, g, a,
-                                                   bk[k], nullptr, nullptr);
+                // the gradient comes from inside the solve, over the kept cluster pairs of its last
+                // truncation (the dense form, sinkhorn_grad_x, pays for every pair of the self term)
+                const GradRequest gr{G, (float)(1.0 / K), k > 0 ? 1 : 0};
+                const int rc = solve_divergence(ctx, x, alpha, N, ys[k], betas[k], Ms[k], D, &Pk, &S, f, g, a,
+                                                bk[k], nullptr, nullptr, last ? nullptr : &gr);
                 if (rc != OTGB_OK && rc != OTGB_ENOCONV) return rc;  // the message is already set
                 Ssum += S;
-                if (!last)
-                    grad_launch(grad_args(x, alpha, N, ys[k], betas[k], Ms[k], D, P.p, eps, a, f, g, G,
-                                          (float)(1.0 / K), k > 0),
-                                st);
             }
             if (S_hist) S_hist[it] = Ssum / K;
             if (last) break;

@@ -94,6 +94,20 @@ struct Solver {
 std::vector<int> make_row_blocks(int n, int block_rows, const std::vector<int> *offsets);
 bool trace_enabled();
 
+// The gradient of S in the points of the first measure, computed inside a
+// solve from its sorted points, final duals and the kept cluster pairs of its
+// last truncation (grad.cu); the barycenter's steps use it.
+struct GradRequest {
+    float *grad;     // N x D, the caller's order
+    float scale;     // multiplies the result
+    int accumulate;  // 1: grad += result, 0: grad = result
+};
+void grad_sparse_launch(const Solver &s, double eps, const GradRequest &gr, cudaStream_t st);
+// sinkhorn_divergence, with an optional gradient request (null: none)
+int solve_divergence(otgb_ctx *ctx, const float *x, const float *a, int N, const float *y, const float *b, int M,
+                     int D, const otgb_params *params, double *cost_host, float *f, float *g, float *a_self,
+                     float *b_self, otgb_plan **plan_out, otgb_stats *stats, const GradRequest *gr);
+
 struct Multiscale {
     double sigma_switch = 0.0;
     int ncl_x = 0, ncl_y = 0;

@@ -482,10 +482,10 @@ void Solver::fine_step(double sigma) {
 
 using namespace otgb;
 
-extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a, int N, const float *y,
-                                   const float *b, int M, int D, const otgb_params *params, double *cost_host,
-                                   float *f, float *g, float *a_self, float *b_self, otgb_plan **plan_out,
-                                   otgb_stats *stats) {
+int otgb::solve_divergence(otgb_ctx *ctx, const float *x, const float *a, int N, const float *y, const float *b,
+                           int M, int D, const otgb_params *params, double *cost_host, float *f, float *g,
+                           float *a_self, float *b_self, otgb_plan **plan_out, otgb_stats *stats,
+                           const GradRequest *gr) {
     if (!ctx) return fail(nullptr, Error{OTGB_EINVAL, "sinkhorn_divergence: null context"});
     try {
         ctx_set_device(ctx);
@@ -633,6 +633,7 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
         }
         OTGB_CUDA_TRY(cudaEventRecord(ctx_event(ctx, 4), st));
         if (rc == OTGB_OK || rc == OTGB_ENOCONV) s.S = s.divergence(s.eps_of(P.blur));
+        if (gr && (rc == OTGB_OK || rc == OTGB_ENOCONV)) grad_sparse_launch(s, s.eps_of(P.blur), *gr, st);
 
         // outputs in the caller's order
         unpermute(s.pf[s.cur], s.X.perm, N, f, st);
@@ -707,6 +708,14 @@ extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a
     } catch (const Error &e) {
         return fail(ctx, e);
     }
+}
+
+extern "C" int sinkhorn_divergence(otgb_ctx *ctx, const float *x, const float *a, int N, const float *y,
+                                   const float *b, int M, int D, const otgb_params *params, double *cost_host,
+                                   float *f, float *g, float *a_self, float *b_self, otgb_plan **plan_out,
+                                   otgb_stats *stats) {
+    return solve_divergence(ctx, x, a, N, y, b, M, D, params, cost_host, f, g, a_self, b_self, plan_out, stats,
+                            nullptr);
 }
 
 extern "C" int otgb_softmin(otgb_ctx *ctx, const float *q, int n_out, const float *p, const float *w,

@@ -8,8 +8,11 @@ expressions of the four duals -- and "Track density atlas").
 * End to end from the GPU's converged duals (float32 duals carry ~1e-6 of
   error, which the exponentials amplify by |C|/eps), at 1e-4.
 * One barycenter step on three small track-density maps equals the step the
-  oracle takes from the same points (its solves and its gradient), and the
-  objective decreases over the iterations."""
+  oracle takes from the same points (its solves and its gradient), single-scale
+  and coarse-to-fine, and the objective decreases over the iterations.
+* In 60-D (fiber bundles, k-means clusters), a barycenter step -- its gradient
+  over the kept cluster pairs of the solve -- equals the step built from the
+  every-pair gradient kernel on the same solve's duals."""
 import numpy as np
 import pytest
 import torch
@@ -103,13 +106,17 @@ def _maps(K=3, n_keep=256):
     return x0, a0, ys, bs
 
 
-def test_barycenter_step_matches_oracle_step(ctx):
+# the barycenter takes its gradients from inside each solve, over the pairs the solve kept: every pair for a
+# single-scale solve, the kept grid-cell pairs for a coarse-to-fine one (each dropped term below e^-27.6 of its row)
+@pytest.mark.parametrize("multiscale", [0, 1])
+def test_barycenter_step_matches_oracle_step(ctx, multiscale):
     from paper_2107_02010_gb300 import otgb
 
     x0, a0, ys, bs = _maps()
     blur, lr = 1.0, 1.0
     eps = blur ** 2
-    p = otgb.default_params(blur=blur, reach=0.0, tol=1e-10, max_iters=20000)
+    p = otgb.default_params(blur=blur, reach=0.0, tol=1e-10, max_iters=20000, multiscale=multiscale, cluster=0,
+                            cell=4.0)
     X = T(x0)
     hist = otgb.sinkhorn_barycenter(ctx, X, T(a0), [T(y) for y in ys], [T(b) for b in bs], p, iters=1, lr=lr)
     G = np.zeros(x0.shape)
@@ -134,3 +141,25 @@ def test_barycenter_objective_decreases(ctx):
     hist = otgb.sinkhorn_barycenter(ctx, T(x0), T(a0), [T(y) for y in ys], [T(b) for b in bs], p, iters=4, lr=1.0)
     print("objective", hist)
     assert all(h1 < h0 for h0, h1 in zip(hist, hist[1:])), hist
+
+
+def test_barycenter_step_60d_kept_pairs_match_every_pair(ctx):
+    from paper_2107_02010_gb300 import otgb
+
+    ctrl = synth.bundle_centrelines()
+    x, a, _ = synth.fiber_bundles(3000, seed=21, ctrl=ctrl, perturb=3.0)
+    y, b, _ = synth.fiber_bundles(2500, seed=22, ctrl=ctrl)
+    blur, reach = 2.0, 20.0
+    p = otgb.default_params(blur=blur, reach=reach, scaling=0.5, multiscale=1, cluster=1, k_clusters=40,
+                            kmeans_iters=10, tol=1e-8, max_iters=5000)
+    X, A, Y, B = T(x), T(a), T(y), T(b)
+    r = otgb.sinkhorn_divergence(ctx, X, A, Y, B, p, want_self=True)
+    stats = r["stats"]
+    assert stats["kept_fraction"] < 0.9, stats["kept_fraction"]  # the truncation drops pairs here
+    G = otgb.sinkhorn_grad_x(ctx, X, A, Y, B, blur ** 2, r["f"], r["g"], r["a_self"])
+    want = (X.double() - G.double() / A.double()[:, None])
+    Xb = X.clone()
+    otgb.sinkhorn_barycenter(ctx, Xb, A, [Y], [B], p, iters=1, lr=1.0)
+    step = float((want - X.double()).abs().max())
+    err = float((Xb.double() - want).abs().max())
+    assert err <= 1e-4 * step + 1e-6, (err, step)
