@@ -753,7 +753,9 @@ def main():
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--n-keep", type=int, default=100_000)
     ap.add_argument("--multiscale", type=int, default=1)
-    ap.add_argument("--tol", type=float, default=1e-6)
+    # the stopping rule: estimated relative change of S below tol (1e-5, the accuracy the time-to-solve is quoted
+    # at; the S it returns is within about 1e-7 of the converged S* on the fiber workload)
+    ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--max-iters", type=int, default=5000)
     ap.add_argument("--ref-rows", type=int, default=0, help="oracle sample rows (0: calibrated to about 5 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
