@@ -440,6 +440,11 @@ def run_density(args):
         o["f"].cpu(), o["g"].cpu()
 
     e2e_ms = e2e_solves(solve_host, args.steps)
+    # S* for the accuracy of the timed solves: the same problem to est. rel. change < 1e-9
+    pstar = density_params(args, otgb)
+    pstar.tol = 1e-9
+    pstar.max_iters = max(args.max_iters, 20000)
+    S_star = otgb.sinkhorn_divergence(ctx, X, A, Y, B, pstar, raise_on_noconv=False)["S"]
     pk = peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     clk = pk.get("sm_max_mhz", 2070.0)
@@ -461,6 +466,8 @@ def run_density(args):
                    "l2": "256 MB buffer written between timed steps (inputs are smaller than L2)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         **s,
+        "S_star": S_star, "rel_err_S": abs(s["S"] - S_star) / abs(S_star),
+        "S_star_from": "the same solve to est. rel. change < 1e-9",
         "roofline": {"bound": "alu", "kernel": "softmin3_tc_kernel (+ fallback)", "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gpairs/s", "frac": achieved / peak,
                      "traffic": TRAFFIC["softmin3_tc_kernel"],
