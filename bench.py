@@ -95,8 +95,10 @@ def density_data(args):
 
 
 def density_params(args, otgb):
+    # the stopping rule is evaluated every 3 steps, as for the fibers (measured at 100k voxels: 91 ms per solve
+    # against 101 ms every 10 steps and 108 ms every step; S within 2e-7 of S* either way)
     return otgb.default_params(blur=1.0, reach=10.0, scaling=0.5, multiscale=int(args.multiscale), cluster=0,
-                               cell=4.0, tol=args.tol, max_iters=args.max_iters, check_every=10,
+                               cell=4.0, tol=args.tol, max_iters=args.max_iters, check_every=3,
                                rows_per_thread=args.rows_per_thread)
 
 
