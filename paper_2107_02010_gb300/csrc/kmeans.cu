@@ -98,6 +98,15 @@ __global__ void __launch_bounds__(kAT) kmeans_assign_kernel(const float *x, int 
     }
 }
 
+// every s-th row (and weight) of x: out row i = x row i s
+__global__ void strided_rows_kernel(const float *x, const float *w, int D, int s, int ni, float *out, float *wout) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)ni * D) return;
+    const size_t i = e / D, d = e - i * D;
+    out[e] = x[i * (size_t)s * D + d];
+    if (w && d == 0) wout[i] = w[i * (size_t)s];
+}
+
 // Weighted mean of each cluster from the points sorted by cluster: CTA k sums
 // its cluster's rows in a fixed order (4 interleaved row groups, combined in a
 // fixed tree), so the centroids do not depend on scheduling.  An empty cluster
@@ -188,7 +197,7 @@ void kmeans_assign(const float *x, int n, int D, const float *cent, int K, int *
 }
 
 KmeansResult kmeans(otgb_ctx *ctx, const std::string &tag, const float *x, const float *w, int n, int D, int K,
-                    int iters, unsigned long long seed, const float *init) {
+                    int iters, unsigned long long seed, const float *init, int sample_max) {
     cudaStream_t st = ctx_stream(ctx);
     Workspace &ws = ctx_ws(ctx);
     const int D4 = (D + 3) & ~3;
@@ -199,14 +208,27 @@ KmeansResult kmeans(otgb_ctx *ctx, const std::string &tag, const float *x, const
     r.labels = ws.get<int>(tag + ":lab", n);
     r.perm = ws.get<int>(tag + ":perm", n);
     r.offsets = ws.get<int>(tag + ":off", K + 1);
+    // the points the Lloyd iterations run on: all of them, or every s-th
+    const float *xi = x, *wi = w;
+    int ni = n;
+    if (sample_max > 0 && n > sample_max) {
+        const int sstep = (n + sample_max - 1) / sample_max;
+        ni = (n + sstep - 1) / sstep;
+        float *xs = ws.get<float>(tag + ":xs", (size_t)ni * D);
+        float *wsub = w ? ws.get<float>(tag + ":ws", ni) : nullptr;
+        strided_rows_kernel<<<(unsigned)(((size_t)ni * D + 255) / 256), 256, 0, st>>>(x, w, D, sstep, ni, xs, wsub);
+        OTGB_CHECK_LAUNCH();
+        xi = xs;
+        wi = wsub;
+    }
     if (init) {
         copy_rows_kernel<<<(K * D4 + 255) / 256, 256, 0, st>>>(init, D, K, r.centroids, D4);
         OTGB_CHECK_LAUNCH();
     } else {
-        std::vector<int> idx = sample_distinct(n, K, seed);
+        std::vector<int> idx = sample_distinct(ni, K, seed);
         int *d_idx = ws.get<int>(tag + ":idx", K);
         OTGB_CUDA_TRY(cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * K, cudaMemcpyHostToDevice, st));
-        gather_rows_kernel<<<(K * D4 + 255) / 256, 256, 0, st>>>(x, D, d_idx, K, r.centroids, D4);
+        gather_rows_kernel<<<(K * D4 + 255) / 256, 256, 0, st>>>(xi, D, d_idx, K, r.centroids, D4);
         OTGB_CHECK_LAUNCH();
         OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // idx is host memory about to go out of scope
     }
@@ -218,23 +240,24 @@ KmeansResult kmeans(otgb_ctx *ctx, const std::string &tag, const float *x, const
     while ((1 << bits) < K) ++bits;
     void *scr = ws.get("sort:scratch", radix_sort_scratch_bytes(n));
     int *sscr = ws.get<int>("scan:scratch", scan_scratch_ints(K + 1) + 64);
-    auto sort_by_label = [&]() {
+    // labels, order and offsets of the first m points of the buffers (m = ni during the iterations, n at the end)
+    auto sort_by_label = [&](int m) {
         OTGB_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (K + 1), st));
-        label_keys_kernel<<<(n + 255) / 256, 256, 0, st>>>(r.labels, n, keys, counts);
+        label_keys_kernel<<<(m + 255) / 256, 256, 0, st>>>(r.labels, m, keys, counts);
         OTGB_CHECK_LAUNCH();
-        radix_sort_pairs(keys, r.perm, n, bits, scr, st);
+        radix_sort_pairs(keys, r.perm, m, bits, scr, st);
         exclusive_scan(counts, excl, K, sscr, st);
         offsets_finish_kernel<<<(K + 255) / 256, 256, 0, st>>>(excl, counts, K, r.offsets);
         OTGB_CHECK_LAUNCH();
     };
     for (int it = 0; it < iters; ++it) {
-        kmeans_assign(x, n, D, r.centroids, K, r.labels, st);
-        sort_by_label();
-        kmeans_segment_mean_kernel<<<K, 256, 0, st>>>(x, w, D, D4, r.perm, r.offsets, r.centroids);
+        kmeans_assign(xi, ni, D, r.centroids, K, r.labels, st);
+        sort_by_label(ni);
+        kmeans_segment_mean_kernel<<<K, 256, 0, st>>>(xi, wi, D, D4, r.perm, r.offsets, r.centroids);
         OTGB_CHECK_LAUNCH();
     }
     kmeans_assign(x, n, D, r.centroids, K, r.labels, st);
-    sort_by_label();
+    sort_by_label(n);
     r.sorted_keys = keys;
     return r;
 }

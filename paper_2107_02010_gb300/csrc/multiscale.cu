@@ -291,9 +291,15 @@ void Multiscale::cluster(Solver &s, const otgb_params &P, const float *x, const 
     } else {
         const int Kx = std::max(1, std::min(P.k_clusters > 0 ? P.k_clusters : s.X.n / 1000, s.X.n));
         const int Ky = std::max(1, std::min(P.k_clusters > 0 ? P.k_clusters : s.Y.n / 1000, s.Y.n));
-        KmeansResult rx = kmeans(s.ctx, "msx", x, a, s.X.n, D, Kx, std::max(0, P.kmeans_iters), P.seed, nullptr);
+        // the Lloyd iterations on at most 131,072 points per side (every s-th point), then one assignment of
+        // all points: at 1M points and 1000 clusters the iterations would otherwise dominate the preparation,
+        // and clusters only decide the truncation's granularity, not the result
+        constexpr int kKmeansSample = 131072;
+        KmeansResult rx = kmeans(s.ctx, "msx", x, a, s.X.n, D, Kx, std::max(0, P.kmeans_iters), P.seed, nullptr,
+                                 kKmeansSample);
         fetch_offsets(rx.offsets, Kx + 1, s.X_off, true);
-        KmeansResult ry = kmeans(s.ctx, "msy", y, b, s.Y.n, D, Ky, std::max(0, P.kmeans_iters), P.seed + 1, nullptr);
+        KmeansResult ry = kmeans(s.ctx, "msy", y, b, s.Y.n, D, Ky, std::max(0, P.kmeans_iters), P.seed + 1, nullptr,
+                                 kKmeansSample);
         fetch_offsets(ry.offsets, Ky + 1, s.Y_off, true);
         s.X.perm = rx.perm;
         s.Y.perm = ry.perm;
