@@ -282,9 +282,13 @@ int sinkhorn_grad_x(otgb_ctx *ctx, const float *x, const float *alpha, int N, co
  * minimises (1/K) sum_k S_{eps,rho}(alpha, beta_k) over the points x of alpha
  * (weights fixed) by `iters` steps of
  *   x_i <- x_i - lr (1/alpha_i) (1/K) sum_k dS(alpha, beta_k)/dx_i,
- * each gradient from a solve of sinkhorn_divergence with *params followed by
- * sinkhorn_grad_x.  With p = 2, lr = 1 and without the debiasing term this is
- * the classical fixed-point update x_i <- mean_k of the barycentric projections.
+ * each gradient computed at the end of a solve of sinkhorn_divergence with
+ * *params (after the first step every solve starts at blur from the previous
+ * step's four duals).  The gradient is the expression of sinkhorn_grad_x.  In
+ * a coarse-to-fine solve it is summed over the kept cluster pairs of the
+ * solve's last truncation; each dropped term is below e^-tau of its row's
+ * total.  With p = 2, lr = 1 and without the debiasing term, this is the
+ * classical fixed-point update x_i <- mean_k of the barycentric projections.
  *   x: N x D device, updated in place; alpha: N device.
  *   ys, betas: HOST arrays of K device pointers (M_k x D points, M_k weights);
  *   Ms: host array of the K sizes.
