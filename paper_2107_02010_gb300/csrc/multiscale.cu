@@ -144,10 +144,14 @@ __device__ __forceinline__ void flat_to_inst(const ListLaunch &L, int f, int &k,
 
 // Kept columns of a block: the union of the keep bits of its row clusters.
 // The columns are sorted by cluster, so every kept cluster J is one range of
-// consecutive columns [off_c[J], off_c[J+1]).  Each thread owns a contiguous
-// range of bit words, so the ranges come out in increasing order.
-// WRITE = false: count the kept columns and clusters; true: write the ranges
-// with their positions (exclusive scans over the threads), then the sentinel.
+// consecutive columns [off_c[J], off_c[J+1]), and a run of kept clusters
+// J, J+1, .., J+k is one range [off_c[J], off_c[J+k+1]).  Each thread owns a
+// contiguous range of bit words and writes one entry per run within them (a
+// run that crosses into the next thread's words continues as a second entry),
+// so the ranges come out in increasing order.
+// WRITE = false: count the kept columns and the entries; true: write the
+// entries with their positions (exclusive scans over the threads), then the
+// sentinel.
 template <bool WRITE>
 __global__ void list_kernel(const __grid_constant__ ListLaunch L) {
     __shared__ int scan[256], sscan2[256];
@@ -157,14 +161,15 @@ __global__ void list_kernel(const __grid_constant__ ListLaunch L) {
     const int cl0 = P.blk_cl[2 * b], cl1 = P.blk_cl[2 * b + 1];
     const int wpt = (L.nwords + blockDim.x - 1) / blockDim.x;
     const int w0 = threadIdx.x * wpt, w1 = min(L.nwords, w0 + wpt);
-    int cnt = 0, nq = 0;
+    int cnt = 0, nq = 0, last = -2;  // last: the previous kept cluster of this thread
     for (int w = w0; w < w1; ++w) {
         unsigned u = 0;
         for (int I = cl0; I < cl1; ++I) u |= P.bits[(size_t)I * L.nwords + w];
-        nq += __popc(u);
         while (u) {
             const int J = w * 32 + __ffs(u) - 1;
             u &= u - 1;
+            nq += J != last + 1;
+            last = J;
             cnt += P.off_c[J + 1] - P.off_c[J];
         }
     }
@@ -190,30 +195,19 @@ __global__ void list_kernel(const __grid_constant__ ListLaunch L) {
     }
     int2 *out = L.rng + L.rng_ptr[blockIdx.x];
     int pos = scan[threadIdx.x] - cnt, q = sscan2[threadIdx.x] - nq;
+    last = -2;
     for (int w = w0; w < w1; ++w) {
         unsigned u = 0;
         for (int I = cl0; I < cl1; ++I) u |= P.bits[(size_t)I * L.nwords + w];
         while (u) {
             const int J = w * 32 + __ffs(u) - 1;
             u &= u - 1;
-            out[q++] = make_int2(P.off_c[J], pos);
+            if (J != last + 1) out[q++] = make_int2(P.off_c[J], pos);
+            last = J;
             pos += P.off_c[J + 1] - P.off_c[J];
         }
     }
     if (threadIdx.x == blockDim.x - 1) out[Q] = make_int2(0, T);
-}
-
-// One CTA per flat block: the block's ranges written out as one column index
-// per position (list[list_ptr[b] + pos]).
-__global__ void expand_kernel(const int *rng_ptr, const int2 *rng, const int *list_ptr, int *list) {
-    const int b = blockIdx.x;
-    const int k0 = rng_ptr[b], k1 = rng_ptr[b + 1] - 1;  // k1: the sentinel
-    int *out = list + list_ptr[b];
-    for (int k = k0; k < k1; ++k) {
-        const int2 e = rng[k];
-        const int len = rng[k + 1].y - e.y;
-        for (int i = threadIdx.x; i < len; i += blockDim.x) out[e.y + i] = e.x + i;
-    }
 }
 
 __global__ void log_kernel(const float *m, int n, float *out) {
@@ -417,8 +411,6 @@ int Multiscale::run_schedule(Solver &s, const otgb_params &P, const std::vector<
             I.omega = 1.0f;
             I.col_rng = nullptr;
             I.rng_ptr = nullptr;
-            I.col_list = nullptr;
-            I.list_ptr = nullptr;
         }
         std::vector<int4> items;
         for (int q = 0; q < 4; ++q) {
@@ -531,29 +523,13 @@ void Multiscale::before_fine_step(Solver &s, double sigma) {
     LL.rng = d_rng;
     list_kernel<true><<<nflat, 256, 0, st>>>(LL);
     OTGB_CHECK_LAUNCH();
-    // D <= 3 (grid cells of a few dozen points, i.e. short ranges): the ranges are also expanded into
-    // one column index per position, which the kernels read instead of walking short ranges
-    int *d_lptr = nullptr, *d_list = nullptr;
-    if (D <= 3) {
-        std::vector<int> lp(nflat + 1);
-        lp[0] = 0;
-        for (int f = 0; f < nflat; ++f) lp[f + 1] = lp[f] + cnt[f];
-        d_lptr = ws.get<int>("ms:listptr", nflat + 1);
-        OTGB_CUDA_TRY(cudaMemcpyAsync(d_lptr, lp.data(), sizeof(int) * (nflat + 1), cudaMemcpyHostToDevice, st));
-        d_list = ws.get<int>("ms:list", (size_t)std::max(lp[nflat], 1));
-        expand_kernel<<<nflat, 256, 0, st>>>(d_ptr, d_rng, d_lptr, d_list);
-        OTGB_CHECK_LAUNCH();
-        OTGB_CUDA_TRY(cudaStreamSynchronize(st));  // lp goes out of scope
-    }
-    // instances walk the ranges (or read the lists); work items split long sequences of kept columns
+    // instances walk the ranges; work items split long sequences of kept columns
     std::vector<std::vector<int>> ncols(4);
     double kept = 0.0, dense = 0.0;
     for (int q = 0; q < 4; ++q) {
         SoftminInst &I = s.launch.inst[q];
         I.rng_ptr = d_ptr + LL.base[q];
         I.col_rng = d_rng;
-        I.list_ptr = d_lptr ? d_lptr + LL.base[q] : nullptr;
-        I.col_list = d_list;
         ncols[q].assign(cnt.begin() + LL.base[q], cnt.begin() + LL.base[q + 1]);
         const std::vector<int> &hb = (q == 0 || q == 3) ? hbx : hby;
         for (int bl = 0; bl < nb[q]; ++bl) kept += (double)cnt[LL.base[q] + bl] * (hb[bl + 1] - hb[bl]);

@@ -131,19 +131,15 @@ struct SoftminInst {
     // Row blocks and their kept columns.  blk_row0[k]..blk_row0[k+1] are the rows
     // of block k.  col_rng == null: every block sees all columns (dense).
     // Otherwise the columns are sorted by cluster and block k sees the kept
-    // clusters as ranges of consecutive columns: entries
+    // clusters as ranges of consecutive columns (one range per run of kept
+    // clusters with consecutive indices): entries
     // col_rng[rng_ptr[k]] .. col_rng[rng_ptr[k+1] - 1] are (first column, its
     // position in the block's sequence of kept columns), increasing; the last
     // entry of a block is a sentinel (0, number of kept columns).  ColWalk
-    // below maps positions to columns.  col_list (when non-null, instead of the
-    // ranges): the same kept columns expanded one index per position, block k's
-    // at col_list[list_ptr[k] .. list_ptr[k+1]) -- cheaper to read where the
-    // clusters are small (grid cells of a few dozen points).
+    // below maps positions to columns.
     const int *blk_row0;
     const int *rng_ptr;
     const int2 *col_rng;
-    const int *list_ptr;
-    const int *col_list;
     // Cluster-tiled tensor-core form (softmin_tcc.cu, coarse-to-fine solves): the column side's points
     // centred at their cluster's centre and split into BF16 tiles of 128 columns (tcc_tiles, 32 KiB per
     // tile: hi then lo, with H_j in K slots 60..63 rewritten every step); tile0[J] .. tile0[J+1] are the
@@ -171,15 +167,9 @@ struct SoftminInst {
 // past a block's sentinel exists.
 constexpr int kRngLook = 8, kRngPad = kRngLook + 1;
 struct ColWalk {
-    const int2 *e = nullptr;  // entry of the range holding the last position (null: dense or list)
-    const int *lst = nullptr; // the block's expanded list, when the instance has one
+    const int2 *e = nullptr;  // entry of the range holding the last position (null: dense)
     int2 cur, nxt;
     __device__ __forceinline__ void start(const SoftminInst &I, int blk, int pos) {
-        if (I.col_list) {
-            lst = I.col_list + I.list_ptr[blk];
-            e = nullptr;
-            return;
-        }
         if (!I.col_rng) {
             e = nullptr;
             return;
@@ -195,7 +185,6 @@ struct ColWalk {
         nxt = e[1];
     }
     __device__ __forceinline__ int at(int pos) {
-        if (lst) return lst[pos];
         if (!e) return pos;
         while (nxt.y <= pos) {
             int2 w[kRngLook];  // the entries after nxt
@@ -225,7 +214,6 @@ struct ColWalk {
 };
 // Number of kept columns of block blk (all columns when dense).
 __device__ __forceinline__ int kept_cols(const SoftminInst &I, int blk) {
-    if (I.col_list) return I.list_ptr[blk + 1] - I.list_ptr[blk];
     return I.col_rng ? I.col_rng[I.rng_ptr[blk + 1] - 1].y : I.n_cols;
 }
 

@@ -209,8 +209,6 @@ void Solver::setup_instances(const std::vector<int> &hx, const std::vector<int> 
         I.blk_row0 = rows_x[k] ? bx : by;
         I.rng_ptr = nullptr;
         I.col_rng = nullptr;
-        I.list_ptr = nullptr;
-        I.col_list = nullptr;
     }
     nblk_x = (int)hx.size() - 1;
     nblk_y = (int)hy.size() - 1;

@@ -14,11 +14,15 @@
 // terms are small for every pair that matters.  The finish adds back exactly
 // the shift the accumulator applied, in double precision.
 //
-// One CTA (4 warps) owns a row block of at most 128 rows (one tensor-memory
+// One CTA (8 warps) owns a row block of at most 128 rows (one tensor-memory
 // lane per row); columns come in tiles of kN.  Column staging is software
 // pipelined: the indices of tile t+2 and the point of tile t+1 are loaded
-// while the tensor core multiplies tile t+1 and the CTA sums tile t.  Every
-// wait is bounded.  Split blocks write partial sums; the CTA that completes a
+// while the tensor core multiplies tile t+1 and the CTA sums tile t.  The
+// indices come from the block's kept ranges (copied into shared memory once
+// per CTA): every kChunkTiles tiles the CTA writes the column index of each
+// position of the next chunk into one of two shared buffers, each thread
+// kPerThr consecutive positions after one binary search.  Every wait is
+// bounded.  Split blocks write partial sums; the CTA that completes a
 // block's last item sums them in item order and finishes the rows.
 #include <cfloat>
 #include <cmath>
@@ -61,6 +65,49 @@ constexpr int kATile = kM * kK * 2;  // 8 KiB
 constexpr int kBTile = kN * kK * 2;
 constexpr uint32_t kTmemCols = kStages * kN <= 32 ? 32u : (kStages * kN <= 64 ? 64u : (kStages * kN <= 128 ? 128u
                                    : (kStages * kN <= 256 ? 256u : 512u)));
+// range entries of a block staged in shared memory; a block with more reads them from global memory
+constexpr int kRngSmem = 1024;
+// positions per expansion chunk (two buffers in flight) and per thread of an expansion
+constexpr int kChunkTiles = 16, kChunk = kChunkTiles * kN, kPerThr = kChunk / kThreads;
+static_assert(kPerThr * kThreads == kChunk && kPerThr % 4 == 0, "an expansion writes whole int4 groups");
+static_assert(kChunkTiles >= kStages + 2, "a chunk is expanded at least one barrier before its first read");
+
+// Word of position q (of a chunk) in the index buffer: 16-byte groups of four positions, group g stored at
+// g ^ ((g >> 2) & 7) (a permutation of each aligned run of eight groups), so that both the expansion's
+// 16-byte stores (a thread writes 16 consecutive positions) and the staging reads (a warp reads 32
+// consecutive positions) are free of bank conflicts.
+__device__ __forceinline__ int idx_word(int q) {
+    const int g = q >> 2;
+    return ((g ^ ((g >> 2) & 7)) << 2) | (q & 3);
+}
+
+// Column index of positions p0 .. p0 + kPerThr - 1 (those below `end`) from one block's range entries
+// r[0 .. n) (the sentinel last, its position above every position asked for): a binary search for the
+// first, then a forward walk.
+template <typename Entries>
+__device__ __forceinline__ void expand_positions(const Entries &r, int n, int p0, int end, int (&v)[kPerThr]) {
+    int lo = 0, hi = n - 2;  // the last real entry
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (r(mid).y <= p0) lo = mid;
+        else hi = mid - 1;
+    }
+    int k = lo;
+    int2 cur = r(k), nxt = r(k + 1);
+#pragma unroll
+    for (int i = 0; i < kPerThr; ++i) {
+        const int pq = p0 + i;
+        v[i] = 0;
+        if (pq < end) {
+            while (nxt.y <= pq && k + 2 < n) {
+                ++k;
+                cur = nxt;
+                nxt = r(k + 1);
+            }
+            v[i] = cur.x + (pq - cur.y);
+        }
+    }
+}
 
 struct Tc3Smem {
     unsigned char a[kATile];
@@ -70,6 +117,8 @@ struct Tc3Smem {
     int bc[2];
     unsigned long long mbar[kStages];
     uint32_t tslot;
+    int2 rng[kRngSmem];
+    alignas(16) int idx[2][kChunk];
 };
 
 // K-major canonical layout of a tile with 32 K-columns: 8-row x 16-byte core
@@ -127,6 +176,21 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
     const float4 *rows4 = reinterpret_cast<const float4 *>(I.rows);
     const float4 *cols4 = reinterpret_cast<const float4 *>(I.cols);
 
+    // ---- the columns of this item: positions [cb, ce) of the block's kept columns; the block's
+    // range entries (the sentinel last) into shared memory, visible after the first barrier below
+    const int nkept = kept_cols(I, blk);
+    int cb = item.z, ce = item.w;
+    OTGB_DCLAMP(cb, 0, nkept + 1);
+    OTGB_DCLAMP(ce, cb, nkept + 1);
+    const int ncol = ce - cb;
+    const int ntiles = (ncol + kN - 1) / kN;
+    const bool ranged = I.col_rng != nullptr;
+    const int nE = ranged ? I.rng_ptr[blk + 1] - I.rng_ptr[blk] : 0;
+    const int2 *rb = ranged ? I.col_rng + I.rng_ptr[blk] : nullptr;
+    const bool rng_local = ranged && nE <= kRngSmem;
+    if (rng_local)
+        for (int q = tid; q < nE; q += kThreads) S.rng[q] = rb[q];
+
     // ---- rows: centre of the block's bounding box, shifts, the row operand
     const bool valid = half == 0 && t < nr;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -145,6 +209,20 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
         tc::mbar_init_fence();
     }
     __syncthreads();
+    // column index of every position of chunk c (tiles c kChunkTiles ..) into S.idx[c & 1]; the
+    // sentinel's position (the block's number of kept columns) exceeds every position of the item
+    auto expand = [&](int ch) {
+        const int q0 = ch * kChunk + tid * kPerThr;  // item-relative position of this thread's first
+        if (!ranged || q0 >= ncol) return;
+        int v[kPerThr];
+        if (rng_local) expand_positions([&](int k) { return S.rng[k]; }, nE, cb + q0, ce, v);
+        else expand_positions([&](int k) { return rb[k]; }, nE, cb + q0, ce, v);
+#pragma unroll
+        for (int i = 0; i < kPerThr / 4; ++i)
+            *reinterpret_cast<int4 *>(&S.idx[ch & 1][idx_word(tid * kPerThr + 4 * i)]) =
+                make_int4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    };
+    expand(0);  // read after the barriers of the row setup
     float c[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -191,23 +269,13 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
                 make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
     }
 
-    // ---- columns of this item
-    const int nkept = kept_cols(I, blk);
-    int cb = item.z, ce = item.w;
-    OTGB_DCLAMP(cb, 0, nkept + 1);
-    OTGB_DCLAMP(ce, cb, nkept + 1);
-    const int ncol = ce - cb;
-    const int ntiles = (ncol + kN - 1) / kN;
-    ColWalk walk;
-    walk.start(I, blk, cb);
-
-    // thread tid < kN stages column tid of each tile
+    // ---- column staging: thread tid < kN stages column tid of each tile
     const bool stager = tid < kN;
     auto load_idx = [&](int tile) -> int {
         const int pp = tile * kN + tid;
         int jj = -1;
         if (stager && tile < ntiles && pp < ncol) {
-            jj = walk.at(cb + pp);
+            jj = ranged ? S.idx[(tile / kChunkTiles) & 1][idx_word((tile % kChunkTiles) * kN + tid)] : cb + pp;
             OTGB_DCLAMP(jj, 0, I.n_cols);
         }
         return jj;
@@ -301,6 +369,11 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
         __syncthreads();
         tc::fence_after();
         if (tid == 0 && ahead < ntiles) issue(ahead % kStages);
+        // chunk c + 1 in the first iteration of chunk c, while the tensor core works: the index of
+        // tile T is read at the top of iteration T - kStages - 1, so the last read of chunk c - 1 (same
+        // buffer) came kStages + 2 iterations before, and the first read of chunk c + 1 comes
+        // kChunkTiles - kStages - 1 >= 1 iterations later, past this iteration's closing barrier
+        if (tt % kChunkTiles == 0 && tt + kChunkTiles < ntiles) expand(tt / kChunkTiles + 1);
         if (!tc::mbar_wait(&S.mbar[buf], (phase_bits >> buf) & 1u)) ok = false;
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
         phase_bits ^= 1u << buf;
