@@ -54,9 +54,10 @@ TC3_TENSOR_FLOP_PER_PAIR = 2 * 32
 TC60_TENSOR_FLOP_PER_PAIR = 3 * 2 * 64
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # dominant kernel of each workload, from one capture of the current kernel
-# (null when the kernel has changed since); see the profile summaries.
+# (null when the kernel has changed since).  softmin3_tc_kernel: a fine step of
+# the track-density workload (100k x 100k), 6,644,224 bytes read, 0 written.
 TRAFFIC = {
-    "softmin3_tc_kernel": None,
+    "softmin3_tc_kernel": 6644224,
     "softmin_gen_kernel": None,
 }
 
