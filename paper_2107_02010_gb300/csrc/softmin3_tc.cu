@@ -141,8 +141,9 @@ __device__ __forceinline__ float ex2f(float x) {
     return y;
 }
 
-// (rounding with integer operations instead, which frees the conversion unit,
-// measured 2 % slower: it costs issue slots)
+// Scalar split for the row operand (once per CTA).  The per-tile column operand
+// uses the packed form below.  (Rounding with integer operations instead, which
+// also frees the MUFU unit, measured 2 % slower: it costs issue slots.)
 __device__ __forceinline__ uint16_t bfbits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ float bfval(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
 
@@ -155,6 +156,23 @@ __device__ __forceinline__ void split3(float v, uint16_t &h, uint16_t &m, uint16
 }
 
 __device__ __forceinline__ uint32_t pk(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+
+// Two values split at once: H, M, L hold the h, m, l pieces of a in their high halves and of b in their low
+// halves.  The packed conversion rounds each half to nearest even, as the scalar one does, so the pieces are
+// those of split3; it runs on its own pipe, leaving the MUFU unit to ex2.
+__device__ __forceinline__ uint32_t bf2(float hi, float lo) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ float hi_val(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+__device__ __forceinline__ float lo_val(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ void split3x2(float a, float b, uint32_t &H, uint32_t &M, uint32_t &L) {
+    H = bf2(a, b);
+    const float ra = a - hi_val(H), rb = b - lo_val(H);
+    M = bf2(ra, rb);
+    L = bf2(ra - hi_val(M), rb - lo_val(M));
+}
 
 constexpr uint16_t kOne = 0x3F80;  // 1.0 in BF16
 
@@ -295,11 +313,13 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
         const float y0 = okc ? rq.x - c[0] : 0.f, y1 = okc ? rq.y - c[1] : 0.f, y2 = okc ? rq.z - c[2] : 0.f;
         const float sq = y0 * y0 + y1 * y1 + y2 * y2;
         const float H = okc ? s * (fmaf(eps, rq.w, rpot) - 0.5f * sq) - Cb : -1e30f;
-        uint16_t h[3], md[3], l[3], hh[3];
-        split3(y0, h[0], md[0], l[0]);
-        split3(y1, h[1], md[1], l[1]);
-        split3(y2, h[2], md[2], l[2]);
-        split3(H, hh[0], hh[1], hh[2]);
+        uint32_t H01, M01, L01, H2h, M2h, L2h;
+        split3x2(y0, y1, H01, M01, L01);
+        split3x2(y2, H, H2h, M2h, L2h);
+        const uint16_t h[3] = {(uint16_t)(H01 >> 16), (uint16_t)H01, (uint16_t)(H2h >> 16)};
+        const uint16_t md[3] = {(uint16_t)(M01 >> 16), (uint16_t)M01, (uint16_t)(M2h >> 16)};
+        const uint16_t l[3] = {(uint16_t)(L01 >> 16), (uint16_t)L01, (uint16_t)(L2h >> 16)};
+        const uint16_t hh[3] = {(uint16_t)H2h, (uint16_t)M2h, (uint16_t)L2h};
         uint32_t w[16];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
