@@ -62,14 +62,21 @@ __device__ __forceinline__ void split3(float v, uint16_t &h, uint16_t &m, uint16
     l = bfbits(r - bfval(m));
 }
 
-// 8 consecutive values -> BF16 hi and lo parts as two 16-byte vectors
+// Two values rounded to BF16 by one packed conversion (its own pipe, not the MUFU unit's): `hi` in the high
+// half, `lo` in the low half, each to nearest even as the scalar conversion rounds.
+__device__ __forceinline__ uint32_t bf2(float hi, float lo) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// 8 consecutive values -> BF16 hi and lo parts as two 16-byte vectors (value 2q in the low half of word q)
 __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo) {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const uint16_t h0 = bfbits(v[2 * q]), h1 = bfbits(v[2 * q + 1]);
-        h[q] = pk(h0, h1);
-        l[q] = pk(bfbits(v[2 * q] - bfval(h0)), bfbits(v[2 * q + 1] - bfval(h1)));
+        h[q] = bf2(v[2 * q + 1], v[2 * q]);
+        l[q] = bf2(v[2 * q + 1] - __uint_as_float(h[q] & 0xFFFF0000u), v[2 * q] - __uint_as_float(h[q] << 16));
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
