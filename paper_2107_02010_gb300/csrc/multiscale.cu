@@ -508,7 +508,7 @@ void Multiscale::before_fine_step(Solver &s, double sigma) {
     std::vector<int> cq(2 * (size_t)nflat), cnt(nflat), ptr(nflat + 1);
     OTGB_CUDA_TRY(cudaMemcpyAsync(cq.data(), LL.counts, sizeof(int) * 2 * nflat, cudaMemcpyDeviceToHost, st));
     OTGB_CUDA_TRY(cudaStreamSynchronize(st));
-    // range entries per block: its kept clusters and a sentinel; kRngPad padding entries after the
+    // range entries per block: one per run of kept clusters, then a sentinel; kRngPad padding entries after the
     // last block keep every entry the walk reads past a sentinel readable
     ptr[0] = 0;
     for (int f = 0; f < nflat; ++f) {

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, OTGB_TC3_MINB) softmin3_tc_kernel(co
         tc::mbar_init_fence();
     }
     __syncthreads();
-    // column index of every position of chunk c (tiles c kChunkTiles ..) into S.idx[c & 1]; the
+    // column index of every position of chunk ch (tiles ch * kChunkTiles ..) into S.idx[ch & 1]; the
     // sentinel's position (the block's number of kept columns) exceeds every position of the item
     auto expand = [&](int ch) {
         const int q0 = ch * kChunk + tid * kPerThr;  // item-relative position of this thread's first
