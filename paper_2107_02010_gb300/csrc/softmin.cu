@@ -502,19 +502,21 @@ __global__ void __launch_bounds__(32 * kW3) softmin3_finalize_kernel(const __gri
 // shared memory while the CTA multiplies tile t; after the products each
 // thread centres and repacks the part of tile t+1 that it copied itself (so
 // the copy needs no barrier), issues the copies of tile t+2 into the slots it
-// just read, and meets the others at one barrier per tile.  The column operand
-// is stored with its 16-byte chunks XOR-swizzled by the k-pair, so both the
-// repacking stores and the operand loads are free of bank conflicts.
+// just read, and meets the others at one barrier per tile.  Each k-pair row of
+// the column operand is padded by 16 bytes (kYS), so that every operand load
+// address is a register plus an immediate and the loads are free of bank
+// conflicts; the repacking stores, once per tile, take a 4-way conflict.
 // TWO = true: an exact-maximum first pass gives each row's shift.
 constexpr int kNTg = 256;
 constexpr int kBM = 128;
 constexpr int kBN = 64;
 constexpr int kKP = 33;       // 32 coordinate pairs + the folded pair
 constexpr int kXS = kBM + 2;  // float2 stride of a k-pair of X (spreads the staging stores over banks)
+constexpr int kYS = kBN + 2;  // float2 stride of a k-pair of the column operand (16-byte aligned rows)
 
 struct GenSmem {
     float2 xs[kKP][kXS];     // X pairs; pair KPD = (1, -m_i)
-    float2 ys[3][kKP][kBN];  // yt pairs, chunk-swizzled; pair KPD = (H_j, 1); three tiles in flight
+    float2 ys[3][kKP][kYS];  // yt pairs (columns 0 .. kBN-1 of each row); pair KPD = (H_j, 1); three tiles in flight
     float raw[kBN][64];      // raw column coordinates of the next tile, as copied
     float rlw[kBN];
     float rpot[kBN];
@@ -559,8 +561,6 @@ __device__ __forceinline__ u64 mul2(u64 a, u64 b) {
     return d;
 }
 
-// physical 16-byte chunk (two columns) of logical chunk c in k-pair kp
-__device__ __forceinline__ int gen_chunk(int c, int kp) { return c ^ ((kp >> 2) & 7); }
 
 template <bool TWO, int KPT>
 __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_constant__ SoftminLaunch L, int D, int D4) {
@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
 
     // copy/repack roles: chunk ch (coordinates 8 ch .. 8 ch + 7) of columns colb and colb + 32
     const int ch = t & 7, colb = t >> 3;
-    // product roles: rows 8 tr .. 8 tr + 7, logical chunks tc and tc + 16 (columns 2 tc, 2 tc + 1, +32)
+    // product roles: rows 8 tr .. 8 tr + 7, 16-byte chunks tc and tc + 16 of a row (columns 2 tc, 2 tc + 1, +32)
     const int tr = t >> 4, tc = t & 15;
 
     auto load_idx = [&](int tile, int (&j)[2]) {
@@ -675,14 +675,14 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int kp = 4 * ch + e;
-                if (kp < KPD) S.ys[buf][kp][2 * gen_chunk(col >> 1, kp) + (col & 1)] = make_float2(v[2 * e], v[2 * e + 1]);
+                if (kp < KPD) S.ys[buf][kp][col] = make_float2(v[2 * e], v[2 * e + 1]);
             }
             sq += __shfl_xor_sync(0xffffffffu, sq, 1);
             sq += __shfl_xor_sync(0xffffffffu, sq, 2);
             sq += __shfl_xor_sync(0xffffffffu, sq, 4);
             if (ch == 0) {
                 const float H = ok ? s * (fmaf(eps, S.rlw[col], S.rpot[col]) - 0.5f * sq) : -INFINITY;
-                S.ys[buf][KPD][2 * gen_chunk(col >> 1, KPD) + (col & 1)] = make_float2(H, 1.f);
+                S.ys[buf][KPD][col] = make_float2(H, 1.f);
             }
         }
     };
@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(kNTg, 2) softmin_gen_kernel(const __grid_const
         const char *xs0 = reinterpret_cast<const char *>(&S.xs[0][tr * 8]);
         const char *ys0 = reinterpret_cast<const char *>(&S.ys[buf][0][0]);
         auto step = [&](int kp, bool first) {
-            const char *yp = ys0 + kp * (kBN * 8) + (gen_chunk(tc, kp) << 4);
+            const char *yp = ys0 + kp * (kYS * 8) + (tc << 4);
             const ulonglong2 y0 = *reinterpret_cast<const ulonglong2 *>(yp);
             const ulonglong2 y1 = *reinterpret_cast<const ulonglong2 *>(yp + 256);
             const u64 yv[4] = {y0.x, y0.y, y1.x, y1.y};
